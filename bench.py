@@ -1,0 +1,322 @@
+"""Benchmark: tomogram build + evaluate on one GB300 (or N replicas).
+
+Workload: the five-level parking structure (5M points over 100 x 100 x 20 m,
+grid 1000 x 1000 at 0.1 m, 40 slices, robot of height 0.5 m, maximum slope
+30 deg, inflation 0.3 m), generated from seed 2.  One step is one
+tct_build_evaluate call: partition of the points, the per-tile slice stack
+(ground, ceiling, costs, inflation, mask, uniqueness bits) and the
+simplification chain, with the points already resident in HBM.  L2 is
+flushed (a 256 MB write) before every timed step; the flush is outside the
+timed interval.
+
+Printed: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tomogram build+eval Mpoints/s & slice-cells/s, % HBM roofline; batched vs plain"
+UNIT = "Mpoints/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["parking", "building"], default="parking")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2403_07631_gb300 import scenes
+    if name == "parking":
+        return scenes.parking_structure()
+    sc = scenes.two_storey_building()
+    sc.n_slices = 12
+    return sc
+
+
+def config_of(sc, params):
+    return {"workload": sc.name, "points": int(len(sc.points)), "grid": [sc.H, sc.W],
+            "res_m": sc.res, "slices": sc.n_slices, "d_s_m": sc.d_s,
+            "robot": {"d_min": params["d_min"], "theta_s": round(params["theta_s"], 6),
+                      "d_inf": params["d_inf"], "d_sm": params["d_sm"]},
+            "seed": sc.meta.get("seed"), "l2": "flushed before each timed step (256 MB write)",
+            "inputs": "resident in HBM"}
+
+
+def algorithmic_bytes(P, N, H, W):
+    # xyz read once, e^G, e^C, c^T (float32) and the mask (uint8) written
+    # once per slice-cell, the keep flags once per slice
+    return 12 * P + 13 * N * H * W + N
+
+
+def stack_bytes(P, N, H, W):
+    # the slice-stack kernel: its outputs, each point's z once, the cell offsets
+    return 13 * N * H * W + 4 * P + 4 * (H * W + 1)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def cpu_baseline(sc, params):
+    """The FP64 oracle as it stands, on the same workload, on the host cores."""
+    import oracle
+    oracle.compile_library()
+    op = {k: params[k] for k in oracle.PARAM_FIELDS}
+    g = oracle.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, 0.0, sc.n_slices)
+    t0 = time.perf_counter()
+    eG, eC, g, _, _ = oracle.build(sc.points, g, True)
+    cT, mask, frag = oracle.evaluate(g, op, eG, eC)
+    oracle.simplify(eG, cT, op["c_b"], frag)
+    dt = time.perf_counter() - t0
+    return {"value": len(sc.points) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": "the full workload once (build, evaluate with fragility bounds, chain)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2403_07631_gb300 import tct
+    tct_params = None
+    try:
+        tct_params = tct.robot_params()
+    except Exception:
+        import math
+        tct_params = dict(d_min=0.5, d_ref=0.65, theta_b=1.7, theta_s=math.tan(math.radians(30)),
+                          theta_p=0.2, c_b=50.0, alpha_d=20.0, alpha_b=20.0, alpha_s=15.0,
+                          d_inf=0.3, d_sm=0.4, patch_radius=2)
+    sc = workload(args.workload)
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sc, tct_params)
+        if i >= args.warmup:
+            times.append(cb["seconds"])
+    t = statistics.mean(times)
+    P, N, H, W = len(sc.points), sc.n_slices, sc.H, sc.W
+    value = P / t / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(sc, tct_params),
+           "slice_cells_per_s": N * H * W / t,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2403_07631_gb300 import build as libbuild
+    from paper_2403_07631_gb300 import tct
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    libbuild.build()
+
+    params = tct.robot_params()
+    sc = workload(args.workload)
+    P, N, H, W = len(sc.points), sc.n_slices, sc.H, sc.W
+    grid = tct.Grid(sc.x0, sc.y0, sc.res, W, H, sc.d_s, N, 0.0, True)
+    pts = torch.from_numpy(sc.points).to(dev)
+    ws, ground, ceil, cost, mask, keep, stats = tct.alloc_outputs(grid, P, dev, params)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tct.tct_build_evaluate(pts, grid, params, ws, ground, ceil, cost, mask, keep, stats)
+
+    tct.tct_timing_enable(True)
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = tct.tct_launch_count()
+    phase = []
+    for i in range(args.steps):
+        flush.fill_(1)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        phase.append(tct.tct_timing_read())
+    torch.cuda.synchronize()
+    launches = tct.tct_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    stack_ms = statistics.mean(p[1] for p in phase)
+    part_ms = statistics.mean(p[0] for p in phase)
+    chain_ms = statistics.mean(p[2] for p in phase)
+
+    # end to end through the public API: pinned host points in, tomogram out
+    h_pts = torch.from_numpy(sc.points).pin_memory()
+    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (ground, ceil, cost, mask, keep)]
+    d_pts = torch.empty_like(pts)
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_pts.copy_(h_pts, non_blocking=True)
+        tct.tct_build_evaluate(d_pts, grid, params, ws, ground, ceil, cost, mask, keep, stats)
+        for h, d in zip(h_out, (ground, ceil, cost, mask, keep)):
+            h.copy_(d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    h2d = h_pts.numel() * 4
+    d2h = sum(h.numel() * h.element_size() for h in h_out)
+    e2e = statistics.mean(e2e_ms)
+
+    st = tct.stats_from(stats)
+    peak, peak_src = measured_peak_gbs()
+    units = P * world
+    value = units / (ms * 1e-3) / 1e6
+    path_gbs = algorithmic_bytes(P, N, H, W) / (ms * 1e-3) / 1e9
+    sb = stack_bytes(P, N, H, W)
+    stack_gbs = sb / (stack_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stack_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                traffic = json.load(f).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(sc, params),
+        "slice_cells_per_s": N * H * W * world / (ms * 1e-3),
+        "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
+                          "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
+                          "peak_source": peak_src},
+        "roofline": {"kernel": "k_stack (per-tile slice stack)", "bound": "hbm",
+                     "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
+                     "traffic": traffic, "algorithmic_bytes": sb, "ms": stack_ms,
+                     "peak_source": peak_src},
+        "phases_ms": {"partition": part_ms, "stack": stack_ms, "chain": chain_ms},
+        "e2e": {"value": units / (e2e * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kept_slices": int(st.n_kept),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, params)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

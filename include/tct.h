@@ -1,0 +1,200 @@
+/*
+ * tct.h -- C ABI of libtct, point-cloud tomography on one GPU.
+ *
+ * Method: Yang et al., "Efficient Global Navigational Planning in 3D
+ * Structures based on Point Cloud Tomography", arXiv 2403.07631.
+ *   Sec. III-A / Alg. 1 lines 1-6   tomogram construction (tct_build)
+ *   Sec. III-B / Eq. 1-6            scene evaluation (tct_evaluate)
+ *   Sec. III-C / Eq. 7-9            slice simplification (tct_evaluate)
+ *   Sec. III-E / Eq. 10             cost and elevation queries (tct_sample_cost)
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named d_* are device pointers; h_* are host pointers.  The
+ *     caller owns every buffer; the library never allocates memory.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream)
+ *     and perform no host synchronisation, so a sequence of calls can be
+ *     captured into a CUDA graph.
+ *   - Layered outputs are dense [n_slices][H][W] row-major; row i runs along
+ *     +y (cell i covers [y0 + i*res, y0 + (i+1)*res)), column j along +x.
+ *   - Return value: TCT_OK (0) or a negative TCT_ERR_* code for errors the
+ *     host can see (bad arguments, too small a workspace, a failed launch).
+ *     Errors only the device can see (non-finite points) are OR-ed into
+ *     tct_stats.status; read the stats after synchronising the stream.
+ *   - Invalid elevations: ground -inf, ceiling +inf (Sec. III-A: a cell with
+ *     no point in the group is invalid).
+ */
+#ifndef TCT_H
+#define TCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
+
+/* ---- status codes ------------------------------------------------------ */
+#define TCT_OK 0
+#define TCT_ERR_INVALID_ARG (-1)       /* NULL pointer, bad size or value    */
+#define TCT_ERR_WORKSPACE_TOO_SMALL (-2)
+#define TCT_ERR_COVERAGE (-3)          /* d_s > d_min, see TCT_ALLOW_COARSE  */
+#define TCT_ERR_UNSUPPORTED (-4)       /* beyond a documented limit          */
+#define TCT_ERR_CUDA (-5)              /* a CUDA call or launch failed       */
+
+/* device-side status bits (tct_stats.status) */
+#define TCT_DEV_NONFINITE 1            /* some points were NaN/inf: skipped  */
+
+/* ---- limits -------------------------------------------------------------- */
+#define TCT_MAX_SLICES 127             /* N; keeps the uniqueness matrix at 128 bits per slice */
+#define TCT_MAX_KERNEL_RADIUS 15       /* inflation window radius in cells   */
+#define TCT_MAX_PATCH_RADIUS 4         /* p_s patch radius in cells          */
+#define TCT_MAX_POINTS 2000000000LL    /* points per call                    */
+
+/* ---- geometry (Sec. III-A) ---------------------------------------------- */
+#define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (Alg. 1 line 1) */
+
+typedef struct tct_grid {
+    float x0, y0;      /* world position of the corner of cell (0,0), m       */
+    float res;         /* r_g, cell size, m                                    */
+    int32_t W, H;      /* columns (along x) and rows (along y)                 */
+    float d_s;         /* slice interval d_s, m                                */
+    float z_min;       /* plane k is at fl32(z_min + (k+1) d_s), k = 0..N-1    */
+    int32_t n_slices;  /* N, 1..TCT_MAX_SLICES                                 */
+    uint32_t flags;    /* TCT_GRID_*                                           */
+} tct_grid;
+
+/* ---- robot and cost parameters (Sec. III-B, Table I) ------------------- */
+#define TCT_KEEP_ENDS 1u               /* always keep the first and last slice   */
+#define TCT_ALLOW_COARSE 2u            /* accept d_s > d_min (breaks Sec. III-A's coverage rule) */
+
+typedef struct tct_params {
+    float d_min, d_ref;                /* Eq. 1: minimum and normal body height, m   */
+    float theta_b, theta_s, theta_p;   /* Eq. 3-4: barrier, slope, step-safety       */
+    float c_b;                         /* c^B, cost of a barrier                     */
+    float alpha_d, alpha_b, alpha_s;   /* Eq. 1, 4, 3 scaling factors                */
+    float d_inf, d_sm;                 /* Eq. 6: inflation and safe-margin radii, m  */
+    int32_t patch_radius;              /* R_p: p_s patch is (2R_p+1)^2 minus centre  */
+    uint32_t flags;                    /* TCT_KEEP_ENDS | TCT_ALLOW_COARSE           */
+} tct_params;
+
+/* ---- device-written statistics ----------------------------------------- */
+typedef struct tct_stats {
+    int32_t status;                    /* OR of TCT_DEV_* bits                       */
+    int32_t n_slices;                  /* N of the last call                         */
+    int64_t n_points;                  /* points read                                */
+    int64_t n_dropped;                 /* finite points outside the grid             */
+    int64_t n_nonfinite;               /* NaN/inf points, skipped                    */
+    float z_min, z_max;                /* over the finite points                     */
+    int32_t n_kept;                    /* slices kept by the simplification          */
+    int32_t reserved;
+    int64_t valid_cells[TCT_MAX_SLICES + 1]; /* per slice: cells with valid ground   */
+    int64_t trav_cells[TCT_MAX_SLICES + 1];  /* per slice: cells with c^T < c^B      */
+} tct_stats;
+
+/* Human-readable text of a TCT_OK / TCT_ERR_* code.  Never NULL. */
+const char *tct_status_string(int status);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int tct_version(void);
+
+/*
+ * Table I defaults (d_min 0.5, d_ref 0.65, theta_b 1.70, theta_s 0.36,
+ * theta_p 0.20, c^B 50, alpha_d 20, alpha_b 20, alpha_s 15) with the Fig. 3
+ * inflation distances (d_inf 0.2, d_sm 0.4) and R_p = 2.  `p` must not be NULL.
+ */
+void tct_params_default(tct_params *p);
+
+/*
+ * Sec. III-A: derive a grid from the bounds of a cloud.  h_bounds6 =
+ * {x_min, y_min, z_min, x_max, y_max, z_max} (e.g. from tct_bounds).  Sets
+ * x0 = x_min, y0 = y_min, W and H so the maximum falls in the last cell,
+ * z_min, and N = the smallest count whose last plane is at or above z_max.
+ * Returns TCT_ERR_UNSUPPORTED when N would exceed TCT_MAX_SLICES.
+ */
+int tct_plan_grid(const float *h_bounds6, float res, float d_s, tct_grid *out);
+
+/*
+ * Bytes of device workspace tct_build / tct_build_evaluate need for n_points
+ * points on `grid`, or tct_evaluate needs when n_points == 0.  `params` may
+ * be NULL.  Returns 0 for an invalid grid.
+ */
+size_t tct_workspace_bytes(const tct_grid *grid, int64_t n_points, const tct_params *params);
+
+/*
+ * Bounds of a cloud: d_out6 receives {x_min, y_min, z_min, x_max, y_max,
+ * z_max} over the finite points (float, device).  d_xyz: n points, `stride`
+ * floats apart (3 = xyz, 4 = xyzw), 16-byte aligned for the vector path.
+ * d_stats (may be NULL) receives n_points, n_nonfinite and TCT_DEV_NONFINITE.
+ */
+int tct_bounds(const float *d_xyz, int64_t n, int32_t stride, float *d_out6,
+               tct_stats *d_stats, tct_stream stream);
+
+/*
+ * Sec. III-A, Alg. 1 lines 1-6: ground and ceiling layers.  For every slice
+ * k and cell: ground = highest point z <= h_k in the cell, ceiling = lowest
+ * point z > h_k, with h_k = fl32(z_min + (k+1) d_s); a point's cell is
+ * (floor(fl32(fl32(y-y0)/res)), floor(fl32(fl32(x-x0)/res))).  Points off the
+ * grid are dropped and counted; non-finite points are skipped and flagged.
+ * d_ground, d_ceil: [N][H][W] float32, written in full.
+ */
+int tct_build(const float *d_xyz, int64_t n, int32_t stride, const tct_grid *grid,
+              void *d_ws, size_t ws_bytes, float *d_ground, float *d_ceil,
+              tct_stats *d_stats, tct_stream stream);
+
+/*
+ * Sec. III-B and III-C on given layers.  Per slice: gradient magnitudes
+ * (Eq. 2, central differences; a cell on the border or next to an invalid
+ * ground is a barrier), terrain cost (Eq. 3-4), interval cost (Eq. 1),
+ * initial cost (Eq. 5; invalid ground -> c^B), inflation (Eq. 6, window of
+ * all taps with K > 0, off-grid taps contribute nothing) into d_cost, and
+ * d_mask = (c^T < c^B).  Then the sequential simplification chain (Eq. 7-9,
+ * Eq. 8 against the last kept slice, Eq. 9 against the next slice) into
+ * d_keep[N] (0/1).  d_ground, d_ceil: [N][H][W]; d_cost [N][H][W] float32;
+ * d_mask [N][H][W] uint8; d_keep [N] uint8.  d_aux, when not NULL, receives
+ * five [N][H][W] float32 layers: m^xy, m^grad, c^I, c^G, c^init.
+ */
+int tct_evaluate(const tct_grid *grid, const tct_params *params, const float *d_ground,
+                 const float *d_ceil, void *d_ws, size_t ws_bytes, float *d_cost,
+                 uint8_t *d_mask, uint8_t *d_keep, float *d_aux, tct_stats *d_stats,
+                 tct_stream stream);
+
+/*
+ * tct_build followed by tct_evaluate in one pass over the slices (the
+ * layers are produced and consumed tile by tile on chip).  Same outputs as
+ * the two calls.
+ */
+int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_grid *grid,
+                       const tct_params *params, void *d_ws, size_t ws_bytes,
+                       float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
+                       uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
+
+/* ---- profiling --------------------------------------------------------- */
+
+/*
+ * Turns per-phase timing on (on != 0) or off for the following calls on the
+ * calling thread's current device.  While on, tct_build, tct_evaluate and
+ * tct_build_evaluate record CUDA events on their stream around each phase
+ * (Sec. IV-A times construction and evaluation separately in the same way).
+ * The events are created by the first call that turns timing on.
+ */
+int tct_timing_enable(int on);
+
+/*
+ * Phase times of the last timed call, in milliseconds: ms[0] the partition
+ * of the points (count, scan, scatter, per-cell sort; 0 for tct_evaluate),
+ * ms[1] the per-tile slice-stack kernel (the elevation kernel for
+ * tct_build), ms[2] the simplification chain.  Blocks until the call's last
+ * event has completed.  Returns the number of values written (<= cap) or a
+ * negative TCT_ERR_* code.
+ */
+int tct_timing_read(float *ms, int cap);
+
+/* Kernels launched by the library since it was loaded (a host-side count). */
+int64_t tct_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCT_H */

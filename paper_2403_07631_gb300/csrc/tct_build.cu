@@ -1,0 +1,479 @@
+// tct_build.cu -- tomogram construction kernels (Sec. III-A, Alg. 1 lines 1-6).
+//
+// The cloud is partitioned by cell with a counting sort:
+//   count    one pass over the points: rasterise, per-cell histogram with
+//            warp-aggregated atomics, bounds of z (ordered-int atomics),
+//            dropped / non-finite counts;
+//   scan     exclusive prefix of the histogram (three small kernels);
+//   scatter  second pass over the points: each z lands in its cell's segment;
+//   sort     each cell's segment is sorted by z (thread per cell).
+// A sorted segment answers every plane with one monotone pointer: the ground
+// of plane h is the last z <= h, the ceiling the first z > h.  The fused
+// per-tile evaluation (tct_stack.cu) consumes the segments directly;
+// k_elevations below writes the two layers for tct_build alone.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "tct_internal.cuh"
+
+namespace tct {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct GridDev {
+    float x0, y0, res, Wf, Hf;
+    int32_t W, H;
+};
+
+GridDev grid_dev(const tct_grid &g) {
+    return GridDev{g.x0, g.y0, g.res, (float)g.W, (float)g.H, g.W, g.H};
+}
+
+// Alg. 1 "rasterize": cell = (floor(fl32(fl32(y-y0)/r)), floor(fl32(fl32(x-x0)/r))).
+__device__ __forceinline__ int cell_of(const GridDev &g, float x, float y) {
+    const float u = __fdiv_rn(__fsub_rn(x, g.x0), g.res);
+    const float v = __fdiv_rn(__fsub_rn(y, g.y0), g.res);
+    if (!(u >= 0.0f && u < g.Wf && v >= 0.0f && v < g.Hf)) return -1;
+    return __float2int_rd(v) * g.W + __float2int_rd(u);
+}
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+    return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+__device__ __forceinline__ float fold_zero(float z) { return z == 0.0f ? 0.0f : z; }
+
+// Loads the 4 consecutive points of group `grp` (points 4*grp .. 4*grp+3).
+// The vector path needs the base 16-byte aligned; n is checked by the caller.
+__device__ __forceinline__ void load4(const float *__restrict__ xyz, int stride, int64_t grp,
+                                      float (&p)[4][3]) {
+    if (stride == 3) {
+        const float4 *v = reinterpret_cast<const float4 *>(xyz) + 3 * grp;
+        const float4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2);
+        p[0][0] = a.x; p[0][1] = a.y; p[0][2] = a.z;
+        p[1][0] = a.w; p[1][1] = b.x; p[1][2] = b.y;
+        p[2][0] = b.z; p[2][1] = b.w; p[2][2] = c.x;
+        p[3][0] = c.y; p[3][1] = c.z; p[3][2] = c.w;
+    } else {
+        const float4 *v = reinterpret_cast<const float4 *>(xyz) + 4 * grp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = __ldg(v + q);
+            p[q][0] = a.x; p[q][1] = a.y; p[q][2] = a.z;
+        }
+    }
+}
+
+__device__ __forceinline__ void load1(const float *__restrict__ xyz, int stride, int64_t i,
+                                      float (&p)[3]) {
+    const float *q = xyz + i * stride;
+    p[0] = __ldg(q); p[1] = __ldg(q + 1); p[2] = __ldg(q + 2);
+}
+
+// Per-block accumulation of the statistics every pass over the points keeps.
+struct PointTally {
+    int32_t zlo, zhi;            // ordered-int keys
+    unsigned long long dropped, nonfinite;
+    __device__ void init() {
+        zlo = float_key(INFINITY);
+        zhi = float_key(-INFINITY);
+        dropped = nonfinite = 0;
+    }
+};
+
+__device__ void flush_tally(PointTally t, int32_t *zkeys, tct_stats *stats, bool with_z) {
+    __shared__ int32_t s_lo[kThreads / 32], s_hi[kThreads / 32];
+    __shared__ unsigned long long s_d[kThreads / 32], s_n[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    t.zlo = __reduce_min_sync(0xffffffffu, t.zlo);
+    t.zhi = __reduce_max_sync(0xffffffffu, t.zhi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t.dropped += __shfl_xor_sync(0xffffffffu, t.dropped, o);
+        t.nonfinite += __shfl_xor_sync(0xffffffffu, t.nonfinite, o);
+    }
+    if (lane == 0) { s_lo[warp] = t.zlo; s_hi[warp] = t.zhi; s_d[warp] = t.dropped; s_n[warp] = t.nonfinite; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t lo = s_lo[0], hi = s_hi[0];
+        unsigned long long d = s_d[0], nf = s_n[0];
+        for (int w = 1; w < kThreads / 32; ++w) {
+            lo = min(lo, s_lo[w]); hi = max(hi, s_hi[w]); d += s_d[w]; nf += s_n[w];
+        }
+        if (with_z) {
+            atomicMin(&zkeys[0], lo);
+            atomicMax(&zkeys[1], hi);
+        }
+        if (d) atomicAdd(reinterpret_cast<unsigned long long *>(&stats->n_dropped), d);
+        if (nf) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->n_nonfinite), nf);
+            atomicOr(&stats->status, TCT_DEV_NONFINITE);
+        }
+    }
+}
+
+// Warp-aggregated update of a per-cell counter: lanes of the warp that hit the
+// same cell are served by one atomic; returns this lane's slot (0-based rank
+// among the lanes of its group, plus the counter value the group saw).
+template <bool kSubtract>
+__device__ __forceinline__ int32_t aggregated_atomic(int32_t *ctr, int cell) {
+    const unsigned active = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int key = cell >= 0 ? cell : -1 - lane;        // off-grid lanes stay alone
+    const unsigned group = __match_any_sync(active, key);
+    const int leader = __ffs(group) - 1;
+    const int rank = __popc(group & ((1u << lane) - 1u));
+    int32_t base = 0;
+    if (cell >= 0 && lane == leader)
+        base = kSubtract ? atomicSub(&ctr[cell], __popc(group)) : atomicAdd(&ctr[cell], __popc(group));
+    base = __shfl_sync(active, base, leader);
+    return kSubtract ? base - 1 - rank : base + rank;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bounds(const float *__restrict__ xyz, int64_t n, int stride, int32_t *keys6,
+         tct_stats *stats) {
+    // keys6: ordered-int min x, y, z then max x, y, z
+    int32_t lo[3], hi[3];
+    unsigned long long bad = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { lo[a] = float_key(INFINITY); hi[a] = float_key(-INFINITY); }
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+        float p[3];
+        load1(xyz, stride, i, p);
+        if (!finite3(p[0], p[1], p[2])) { ++bad; continue; }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int32_t k = float_key(fold_zero(p[a]));
+            lo[a] = min(lo[a], k); hi[a] = max(hi[a], k);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+        hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { atomicMin(&keys6[a], lo[a]); atomicMax(&keys6[3 + a], hi[a]); }
+        if (bad && stats) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->n_nonfinite), bad);
+            atomicOr(&stats->status, TCT_DEV_NONFINITE);
+        }
+    }
+}
+
+__global__ void k_bounds_init(int32_t *keys6, tct_stats *stats, int64_t n) {
+    if (threadIdx.x < 3) {
+        keys6[threadIdx.x] = float_key(INFINITY);
+        keys6[3 + threadIdx.x] = float_key(-INFINITY);
+    }
+    if (threadIdx.x == 0 && stats) stats->n_points = n;
+}
+
+// Converts the ordered-int keys held in out6 back to floats, in place.
+__global__ void k_bounds_finish(float *out6, tct_stats *stats) {
+    const int t = threadIdx.x;
+    int32_t k = 0;
+    if (t < 6) k = reinterpret_cast<const int32_t *>(out6)[t];
+    __syncwarp();
+    if (t < 6) out6[t] = key_float(k);
+    if (t == 2 && stats) stats->z_min = key_float(k);
+    if (t == 5 && stats) stats->z_max = key_float(k);
+}
+
+// Pass 1: histogram of points per cell plus the z bounds and tallies.
+__global__ void __launch_bounds__(kThreads)
+k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
+        int32_t *__restrict__ cnt, int32_t *zkeys, tct_stats *stats) {
+    PointTally t;
+    t.init();
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ngroups = vec ? n / 4 : 0;
+    auto visit = [&](float x, float y, float z) {
+        int cell = -1;
+        if (!finite3(x, y, z)) {
+            ++t.nonfinite;
+        } else {
+            const int32_t k = float_key(fold_zero(z));
+            t.zlo = min(t.zlo, k); t.zhi = max(t.zhi, k);
+            cell = cell_of(g, x, y);
+            if (cell < 0) ++t.dropped;
+        }
+        aggregated_atomic<false>(cnt, cell);
+    };
+    // the loop bound is warp-uniform so that every lane joins each match
+    for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
+        const int64_t grp = base + (threadIdx.x & 31);
+        float p[4][3];
+        const bool ok = grp < ngroups;
+        if (ok) load4(xyz, stride, grp, p);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (ok) visit(p[q][0], p[q][1], p[q][2]);
+            else aggregated_atomic<false>(cnt, -1);
+        }
+    }
+    for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
+        const int64_t i = base + (threadIdx.x & 31);
+        if (i < n) {
+            float p[3];
+            load1(xyz, stride, i, p);
+            visit(p[0], p[1], p[2]);
+        } else {
+            aggregated_atomic<false>(cnt, -1);
+        }
+    }
+    flush_tally(t, zkeys, stats, true);
+}
+
+// Pass 2: every finite on-grid point writes its z into its cell's segment.
+// Slots are taken from the top of the segment down, so cnt returns to zero.
+__global__ void __launch_bounds__(kThreads)
+k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
+          int32_t *__restrict__ cnt, const int32_t *__restrict__ start, float *__restrict__ zs) {
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ngroups = vec ? n / 4 : 0;
+    auto visit = [&](float x, float y, float z) {
+        const int cell = finite3(x, y, z) ? cell_of(g, x, y) : -1;
+        const int32_t slot = aggregated_atomic<true>(cnt, cell);
+        if (cell >= 0) zs[start[cell] + slot] = fold_zero(z);
+    };
+    for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
+        const int64_t grp = base + (threadIdx.x & 31);
+        float p[4][3];
+        const bool ok = grp < ngroups;
+        if (ok) load4(xyz, stride, grp, p);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (ok) visit(p[q][0], p[q][1], p[q][2]);
+            else aggregated_atomic<true>(cnt, -1);
+        }
+    }
+    for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
+        const int64_t i = base + (threadIdx.x & 31);
+        if (i < n) {
+            float p[3];
+            load1(xyz, stride, i, p);
+            visit(p[0], p[1], p[2]);
+        } else {
+            aggregated_atomic<true>(cnt, -1);
+        }
+    }
+}
+
+// Exclusive scan of cnt[0, m) into start[0, m], in tiles of kScanTile.
+constexpr int kPerThread = kScanTile / kThreads;   // 16
+
+__global__ void __launch_bounds__(kThreads)
+k_scan_reduce(const int32_t *__restrict__ cnt, int64_t m, int32_t *__restrict__ partial) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kPerThread;
+    int32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q)
+        if (base + q < m) s += cnt[base + q];
+    s = __reduce_add_sync(0xffffffffu, s);
+    __shared__ int32_t ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_partials(int32_t *partial, int nb) {
+    // one block; each thread owns a contiguous run of the block sums
+    __shared__ int32_t ws[32];
+    const int per = (nb + 1023) / 1024;
+    const int lo = threadIdx.x * per;
+    int32_t s = 0;
+    for (int q = 0; q < per; ++q)
+        if (lo + q < nb) s += partial[lo + q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    int32_t run = x - s + (warp > 0 ? ws[warp - 1] : 0);
+    for (int q = 0; q < per; ++q) {
+        if (lo + q < nb) {
+            const int32_t v = partial[lo + q];
+            partial[lo + q] = run;
+            run += v;
+        }
+    }
+    if (threadIdx.x == 1023) partial[nb] = run;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restrict__ partial,
+            int32_t *__restrict__ start, int nb) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kPerThread;
+    int32_t v[kPerThread];
+    int32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) {
+        v[q] = base + q < m ? cnt[base + q] : 0;
+        s += v[q];
+    }
+    __shared__ int32_t ws[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    int32_t off = partial[blockIdx.x] + x - s;
+    for (int w = 0; w < warp; ++w) off += ws[w];
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) {
+        if (base + q < m) start[base + q] = off;
+        off += v[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[m] = partial[nb];
+}
+
+// Sort each cell's segment ascending (insertion sort; segments are short).
+__global__ void __launch_bounds__(kThreads)
+k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ zs) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    const int32_t s = start[c], e = start[c + 1];
+    for (int32_t i = s + 1; i < e; ++i) {
+        const float v = zs[i];
+        int32_t j = i - 1;
+        while (j >= s && zs[j] > v) { zs[j + 1] = zs[j]; --j; }
+        zs[j + 1] = v;
+    }
+}
+
+__global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices) {
+    if (threadIdx.x == 0) {
+        zkeys[0] = float_key(INFINITY);
+        zkeys[1] = float_key(-INFINITY);
+        stats->n_points = n;
+        stats->n_slices = n_slices;
+    }
+}
+
+__global__ void k_partition_finish(const int32_t *zkeys, tct_stats *stats) {
+    if (threadIdx.x == 0) {
+        stats->z_min = key_float(zkeys[0]);
+        stats->z_max = key_float(zkeys[1]);
+    }
+}
+
+// tct_build alone: thread per cell walks the slices with the monotone pointer.
+__global__ void __launch_bounds__(kThreads)
+k_elevations(const int32_t *__restrict__ start, const float *__restrict__ zs, int64_t m,
+             int n_slices, float d_s, float z_min_given, bool zmin_from_data,
+             const int32_t *__restrict__ zkeys, float *__restrict__ ground,
+             float *__restrict__ ceil) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    float z_min = z_min_given;
+    if (zmin_from_data) {
+        z_min = key_float(zkeys[0]);
+        if (!isfinite(z_min)) z_min = 0.0f;
+    }
+    int32_t p = start[c];
+    const int32_t e = start[c + 1];
+    float zg = -INFINITY;
+    float zc = p < e ? zs[p] : INFINITY;
+    for (int k = 0; k < n_slices; ++k) {
+        const float h = __fmaf_rn((float)(k + 1), d_s, z_min);
+        while (zc <= h) {
+            zg = zc;
+            ++p;
+            zc = p < e ? zs[p] : INFINITY;
+        }
+        __stcs(&ground[(int64_t)k * m + c], zg);
+        __stcs(&ceil[(int64_t)k * m + c], zc);
+    }
+}
+
+int grid_blocks(int64_t work_items, int per_block) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t b = (work_items + per_block - 1) / per_block;
+    int64_t cap = (int64_t)sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_bounds(const float *xyz, int64_t n, int stride, float *out6, tct_stats *stats,
+                          cudaStream_t s) {
+    int32_t *keys6 = reinterpret_cast<int32_t *>(out6);
+    k_bounds_init<<<1, 32, 0, s>>>(keys6, stats, n);
+    if (n > 0) k_bounds<<<grid_blocks(n, kThreads * 4), kThreads, 0, s>>>(xyz, n, stride, keys6, stats);
+    k_bounds_finish<<<1, 32, 0, s>>>(out6, stats);
+    count_launches(n > 0 ? 3 : 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_grid &g,
+                             const Workspace &ws, tct_stats *stats, cudaStream_t s) {
+    const int64_t m = (int64_t)g.W * g.H;
+    const GridDev gd = grid_dev(g);
+    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
+    cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int32_t) * m, s);
+    if (e != cudaSuccess) return e;
+    k_partition_init<<<1, 32, 0, s>>>(ws.zkeys, stats, n, g.n_slices);
+    const int64_t work = vec ? n / 4 + 1 : n;
+    if (n > 0)
+        k_count<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
+                                                                 ws.zkeys, stats);
+    k_partition_finish<<<1, 32, 0, s>>>(ws.zkeys, stats);
+    const int nb = (int)((m + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
+    k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
+    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
+    if (n > 0)
+        k_scatter<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
+                                                                   ws.start, ws.zs);
+    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(ws.start, m, ws.zs);
+    count_launches(n > 0 ? 8 : 6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *ground, float *ceil,
+                              cudaStream_t s) {
+    const int64_t m = (int64_t)g.W * g.H;
+    k_elevations<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        ws.start, ws.zs, m, g.n_slices, g.d_s, g.z_min, (g.flags & TCT_GRID_ZMIN_FROM_DATA) != 0,
+        ws.zkeys, ground, ceil);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace tct

@@ -1,0 +1,83 @@
+// tct_internal.cuh -- private declarations shared by the libtct translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tct.h"
+
+namespace tct {
+
+constexpr int kMaxK = 2 * TCT_MAX_KERNEL_RADIUS + 1;
+
+// Order-preserving map between float and int32 (non-NaN floats): a < b as
+// floats iff key(a) < key(b) as signed ints.
+__host__ __device__ __forceinline__ int32_t float_key(float f) {
+#ifdef __CUDA_ARCH__
+    int32_t i = __float_as_int(f);
+#else
+    union { float f; int32_t i; } u; u.f = f; int32_t i = u.i;
+#endif
+    return i ^ ((i >> 31) & 0x7fffffff);
+}
+__host__ __device__ __forceinline__ float key_float(int32_t k) {
+    int32_t i = k ^ ((k >> 31) & 0x7fffffff);
+#ifdef __CUDA_ARCH__
+    return __int_as_float(i);
+#else
+    union { float f; int32_t i; } u; u.i = i; return u.f;
+#endif
+}
+
+// Workspace carved from the caller's buffer; offsets are 256-byte aligned.
+struct Workspace {
+    int32_t *cnt;       // [HW]   points per cell (zero between builds)
+    int32_t *start;     // [HW+1] exclusive prefix of cnt
+    int32_t *partial;   // [n_scan_blocks + 1]
+    float *zs;          // [P]    point heights grouped by cell, sorted per cell
+    int32_t *zkeys;     // [2]    ordered-int min / max z of the finite points
+    int32_t *upre;      // [128]  per slice: bits [0, upre) of the uniqueness row set
+    uint32_t *ubits;    // [128][4] per slice: further uniqueness bits
+    tct_stats *stats;   // fallback stats block when the caller passes none
+    size_t bytes;
+};
+
+constexpr int kScanTile = 4096;   // cells per scan block
+
+Workspace carve(void *base, const tct_grid &g, int64_t n_points);
+
+// Inflation kernel and per-call constants of Sec. III-B in float32.
+struct EvalConsts {
+    float d_min, d_ref, theta_b, theta_s, c_b, alpha_d, alpha_b, alpha_s;
+    float inv2r;        // 1 / (2 r_g)
+    float inv_ts;       // 1 / theta_s
+    float inv_tb;       // 1 / theta_b
+    int32_t patch_radius;
+    int32_t count_thresh;   // p_s > theta_p  <=>  gentle count > count_thresh
+    int32_t rk;             // inflation window radius
+    uint32_t flags;
+    float K[kMaxK * kMaxK]; // weights, row-major (n, m), (2 rk + 1)^2 used
+};
+
+int make_eval_consts(const tct_grid &g, const tct_params &p, EvalConsts *c);
+
+// Host-side count of kernel launches (tct_launch_count).
+void count_launches(int n);
+
+// launchers (tct_build.cu)
+cudaError_t launch_bounds(const float *xyz, int64_t n, int stride, float *out6,
+                          tct_stats *stats, cudaStream_t s);
+cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_grid &g,
+                             const Workspace &ws, tct_stats *stats, cudaStream_t s);
+cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *ground,
+                              float *ceil, cudaStream_t s);
+
+// launchers (tct_stack.cu)
+cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
+                         const int32_t *zkeys, const float *gin, const float *cin,
+                         float *ground, float *ceil, float *cost, uint8_t *mask, float *aux,
+                         int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s);
+cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits,
+                         uint32_t flags, uint8_t *keep, tct_stats *stats, cudaStream_t s);
+
+}  // namespace tct

@@ -1,0 +1,269 @@
+"""Python binding of libtct (include/tct.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch
+tensors for the device buffers; the work runs in the library's CUDA kernels
+on the current torch stream.  There is no fallback: if libtct.so has not
+been built (``paper_2403_07631_gb300.build``) or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+MAX_SLICES = 127
+OK = 0
+GRID_ZMIN_FROM_DATA = 1
+KEEP_ENDS = 1
+ALLOW_COARSE = 2
+DEV_NONFINITE = 1
+
+
+class TctGrid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_float), ("y0", ctypes.c_float), ("res", ctypes.c_float),
+                ("W", ctypes.c_int32), ("H", ctypes.c_int32), ("d_s", ctypes.c_float),
+                ("z_min", ctypes.c_float), ("n_slices", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class TctParams(ctypes.Structure):
+    _fields_ = [("d_min", ctypes.c_float), ("d_ref", ctypes.c_float),
+                ("theta_b", ctypes.c_float), ("theta_s", ctypes.c_float),
+                ("theta_p", ctypes.c_float), ("c_b", ctypes.c_float),
+                ("alpha_d", ctypes.c_float), ("alpha_b", ctypes.c_float),
+                ("alpha_s", ctypes.c_float), ("d_inf", ctypes.c_float), ("d_sm", ctypes.c_float),
+                ("patch_radius", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class TctStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("n_points", ctypes.c_int64), ("n_dropped", ctypes.c_int64),
+                ("n_nonfinite", ctypes.c_int64), ("z_min", ctypes.c_float),
+                ("z_max", ctypes.c_float), ("n_kept", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("valid_cells", ctypes.c_int64 * (MAX_SLICES + 1)),
+                ("trav_cells", ctypes.c_int64 * (MAX_SLICES + 1))]
+
+
+STATS_BYTES = ctypes.sizeof(TctStats)
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "tct_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tct_version": (ctypes.c_int, []),
+    "tct_params_default": (None, [ctypes.POINTER(TctParams)]),
+    "tct_plan_grid": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.POINTER(TctGrid)]),
+    "tct_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TctGrid), ctypes.c_int64,
+                                              ctypes.POINTER(TctParams)]),
+    "tct_bounds": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P]),
+    "tct_build": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(TctGrid),
+                                 _P, ctypes.c_size_t, _P, _P, _P, _P]),
+    "tct_evaluate": (ctypes.c_int, [ctypes.POINTER(TctGrid), ctypes.POINTER(TctParams), _P, _P,
+                                    _P, ctypes.c_size_t, _P, _P, _P, _P, _P, _P]),
+    "tct_build_evaluate": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(TctGrid), ctypes.POINTER(TctParams), _P,
+                                          ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P]),
+    "tct_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+    "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tct_launch_count": (ctypes.c_int64, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libtct.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libtct.so is not built ({_build.LIB}); run "
+                               "paper_2403_07631_gb300.build.build() first")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class TctError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        msg = load().tct_status_string(status).decode()
+        super().__init__(f"{fn} failed: {msg} ({status})")
+        self.status = status
+
+
+def _check(fn: str, status: int):
+    if status != OK:
+        raise TctError(fn, status)
+
+
+# ------------------------------------------------------------- value types
+
+@dataclass
+class Grid:
+    """Tomogram geometry (tct_grid)."""
+    x0: float
+    y0: float
+    res: float
+    W: int
+    H: int
+    d_s: float
+    n_slices: int
+    z_min: float = 0.0
+    zmin_from_data: bool = True
+
+    def c(self) -> TctGrid:
+        return TctGrid(self.x0, self.y0, self.res, self.W, self.H, self.d_s, self.z_min,
+                       self.n_slices, GRID_ZMIN_FROM_DATA if self.zmin_from_data else 0)
+
+    @property
+    def shape(self):
+        return (self.n_slices, self.H, self.W)
+
+
+def params_default() -> dict:
+    """tct_params_default: Table I with the Fig. 3 inflation distances."""
+    p = TctParams()
+    load().tct_params_default(ctypes.byref(p))
+    return {f: getattr(p, f) for f, _ in TctParams._fields_}
+
+
+def robot_params() -> dict:
+    """The benchmark robot: height 0.5 m, max slope 30 deg, inflation 0.3 m."""
+    p = params_default()
+    p.update(theta_s=math.tan(math.radians(30.0)), d_inf=0.3, d_sm=0.4)
+    return p
+
+
+def _params_c(p: dict) -> TctParams:
+    full = {"flags": 0}
+    full.update(p)
+    return TctParams(*[full[f] for f, _ in TctParams._fields_])
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _points(xyz: torch.Tensor):
+    if xyz.dtype != torch.float32 or xyz.dim() != 2 or xyz.shape[1] not in (3, 4):
+        raise ValueError("points must be a [P,3] or [P,4] float32 tensor")
+    if not xyz.is_contiguous():
+        raise ValueError("points must be contiguous")
+    return xyz.shape[0], xyz.shape[1]
+
+
+# ------------------------------------------------------------ entry points
+
+def tct_version() -> int:
+    return load().tct_version()
+
+
+def tct_status_string(status: int) -> str:
+    return load().tct_status_string(status).decode()
+
+
+def tct_plan_grid(bounds6, res: float, d_s: float) -> Grid:
+    """Grid over the cloud bounds {x_min, y_min, z_min, x_max, y_max, z_max}."""
+    b = (ctypes.c_float * 6)(*[float(v) for v in bounds6])
+    g = TctGrid()
+    _check("tct_plan_grid", load().tct_plan_grid(ctypes.cast(b, _P), res, d_s, ctypes.byref(g)))
+    return Grid(g.x0, g.y0, g.res, g.W, g.H, g.d_s, g.n_slices, g.z_min, True)
+
+
+def tct_workspace_bytes(grid: Grid, n_points: int, params: dict | None = None) -> int:
+    cp = _params_c(params) if params else None
+    n = load().tct_workspace_bytes(ctypes.byref(grid.c()), n_points,
+                                   ctypes.byref(cp) if cp else None)
+    if n == 0:
+        raise TctError("tct_workspace_bytes", -1)
+    return n
+
+
+def tct_bounds(xyz: torch.Tensor, out6: torch.Tensor, stats: torch.Tensor | None = None):
+    n, stride = _points(xyz)
+    _check("tct_bounds", load().tct_bounds(_ptr(xyz), n, stride, _ptr(out6), _ptr(stats), _stream()))
+
+
+def tct_build(xyz: torch.Tensor, grid: Grid, ws: torch.Tensor, ground: torch.Tensor,
+              ceil: torch.Tensor, stats: torch.Tensor | None = None):
+    n, stride = _points(xyz)
+    _check("tct_build", load().tct_build(_ptr(xyz), n, stride, ctypes.byref(grid.c()), _ptr(ws),
+                                         ws.numel() * ws.element_size(), _ptr(ground), _ptr(ceil),
+                                         _ptr(stats), _stream()))
+
+
+def tct_evaluate(grid: Grid, params: dict, ground: torch.Tensor, ceil: torch.Tensor,
+                 ws: torch.Tensor, cost: torch.Tensor, mask: torch.Tensor, keep: torch.Tensor,
+                 aux: torch.Tensor | None = None, stats: torch.Tensor | None = None):
+    cp = _params_c(params)
+    _check("tct_evaluate", load().tct_evaluate(ctypes.byref(grid.c()), ctypes.byref(cp),
+                                               _ptr(ground), _ptr(ceil), _ptr(ws),
+                                               ws.numel() * ws.element_size(), _ptr(cost),
+                                               _ptr(mask), _ptr(keep), _ptr(aux), _ptr(stats),
+                                               _stream()))
+
+
+def tct_build_evaluate(xyz: torch.Tensor, grid: Grid, params: dict, ws: torch.Tensor,
+                       ground: torch.Tensor, ceil: torch.Tensor, cost: torch.Tensor,
+                       mask: torch.Tensor, keep: torch.Tensor, stats: torch.Tensor | None = None):
+    n, stride = _points(xyz)
+    cp = _params_c(params)
+    _check("tct_build_evaluate",
+           load().tct_build_evaluate(_ptr(xyz), n, stride, ctypes.byref(grid.c()),
+                                     ctypes.byref(cp), _ptr(ws), ws.numel() * ws.element_size(),
+                                     _ptr(ground), _ptr(ceil), _ptr(cost), _ptr(mask), _ptr(keep),
+                                     _ptr(stats), _stream()))
+
+
+# --------------------------------------------------------------- helpers
+
+def stats_from(t: torch.Tensor) -> TctStats:
+    """Copy a device stats block (uint8 tensor of STATS_BYTES) into a TctStats."""
+    host = t.detach().to("cpu").numpy().tobytes()
+    return TctStats.from_buffer_copy(host)
+
+
+def alloc_outputs(grid: Grid, n_points: int, device="cuda", params: dict | None = None):
+    """Device buffers for tct_build_evaluate: (ws, ground, ceil, cost, mask, keep, stats)."""
+    shape = grid.shape
+    ws = torch.empty(tct_workspace_bytes(grid, n_points, params), dtype=torch.uint8, device=device)
+    ground = torch.empty(shape, dtype=torch.float32, device=device)
+    ceil = torch.empty(shape, dtype=torch.float32, device=device)
+    cost = torch.empty(shape, dtype=torch.float32, device=device)
+    mask = torch.empty(shape, dtype=torch.uint8, device=device)
+    keep = torch.empty(grid.n_slices, dtype=torch.uint8, device=device)
+    stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
+    return ws, ground, ceil, cost, mask, keep, stats
+
+
+def tct_timing_enable(on: bool = True):
+    _check("tct_timing_enable", load().tct_timing_enable(1 if on else 0))
+
+
+def tct_timing_read() -> list[float]:
+    """Phase times (ms) of the last timed call: partition, slice stack, chain."""
+    buf = (ctypes.c_float * 3)()
+    n = load().tct_timing_read(ctypes.cast(buf, _P), 3)
+    if n < 0:
+        raise TctError("tct_timing_read", n)
+    return [float(buf[i]) for i in range(n)]
+
+
+def tct_launch_count() -> int:
+    return int(load().tct_launch_count())

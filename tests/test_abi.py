@@ -1,0 +1,87 @@
+"""The C ABI: libtct.so builds for sm_103a, loads without a GPU and exports
+every entry point include/tct.h declares; host-only calls behave as the
+header documents (no kernel is launched here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tct.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[a-z_ ]*?[a-z_0-9]+\s*\*?\s*(tct_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_07631_gb300 import build, tct
+    build.build()
+    return tct.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("tct_build", "tct_evaluate", "tct_build_evaluate", "tct_bounds",
+              "tct_workspace_bytes", "tct_plan_grid", "tct_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), f"libtct.so does not export {n}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2403_07631_gb300 import tct
+    for n in declared_functions():
+        assert n in tct._SIGNATURES, f"binding lacks {n}"
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2403_07631_gb300 import tct
+    assert ctypes.sizeof(tct.TctGrid) == 36
+    assert ctypes.sizeof(tct.TctParams) == 52
+    assert ctypes.sizeof(tct.TctStats) == 48 + 2 * 8 * 128
+
+
+def test_host_only_calls(lib):
+    from paper_2403_07631_gb300 import tct
+    assert tct.tct_status_string(0) == "ok"
+    assert "workspace" in tct.tct_status_string(-2)
+    p = tct.params_default()
+    assert p["c_b"] == 50.0 and p["patch_radius"] == 2
+    g = tct.tct_plan_grid([0.0, 0.0, -0.0499, 19.99, 19.95, 5.84], 0.1, 0.5)
+    assert (g.W, g.H, g.n_slices) == (200, 200, 12)
+    with pytest.raises(tct.TctError):
+        tct.tct_plan_grid([0.0, 0.0, 0.0, 1.0, 1.0, 1000.0], 0.1, 0.5)   # N > 127
+    n = tct.tct_workspace_bytes(tct.Grid(0.0, 0.0, 0.1, 1000, 1000, 0.5, 40), 5_000_000)
+    assert n >= 4 * 5_000_000 + 8 * 1_000_000
+    with pytest.raises(tct.TctError):
+        tct.tct_workspace_bytes(tct.Grid(0.0, 0.0, -0.1, 10, 10, 0.5, 4), 10)
+
+
+def test_argument_errors_need_no_gpu(lib):
+    from paper_2403_07631_gb300 import tct
+    g = tct.Grid(0.0, 0.0, 0.1, 10, 10, 0.5, 4).c()
+    P = tct.TctParams(**{k: v for k, v in tct.params_default().items()})
+    # NULL buffers and a too-small workspace are refused before any launch
+    rc = lib.tct_build_evaluate(None, 10, 3, ctypes.byref(g), ctypes.byref(P), None, 0,
+                                None, None, None, None, None, None, None)
+    assert rc == -1
+    fake = ctypes.c_void_p(256)
+    rc = lib.tct_build_evaluate(fake, 10, 3, ctypes.byref(g), ctypes.byref(P), fake, 16,
+                                fake, fake, fake, fake, fake, None, None)
+    assert rc == -2
+    rc = lib.tct_build_evaluate(fake, 10, 5, ctypes.byref(g), ctypes.byref(P), fake, 1 << 30,
+                                fake, fake, fake, fake, fake, None, None)
+    assert rc == -1
+    g.n_slices = 200
+    rc = lib.tct_evaluate(ctypes.byref(g), ctypes.byref(P), fake, fake, fake, 1 << 30,
+                          fake, fake, fake, None, None, None)
+    assert rc == -4

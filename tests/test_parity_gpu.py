@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on
+the same seeded inputs, element by element (tolerances in tests/_parity.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from conftest import PARAMS_ROBOT, PARAMS_TABLE1  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import _parity as P  # noqa: E402
+from paper_2403_07631_gb300 import scenes, tct  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_07631_gb300 import build
+    build.build()
+    import oracle
+    oracle.compile_library()
+
+
+def _grid_of(sc, n_slices=None, zmin_from_data=True, z_min=0.0):
+    return tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s,
+                    n_slices if n_slices else sc.n_slices, z_min, zmin_from_data)
+
+
+def _full_check(points, grid, params, stride=3, misalign=False):
+    g = P.gpu_build_evaluate(points, grid, params, stride=stride, misalign=misalign)
+    r = P.oracle_all(points, grid, params)
+    P.assert_equal_layers(g["ground"], r["ground"], "ground")
+    P.assert_equal_layers(g["ceil"], r["ceil"], "ceiling")
+    P.assert_costs(g["cost"], r["cost"], r["fragile"])
+    P.assert_masks(g["mask"], r["mask"], r["fragile"])
+    P.assert_keep(g["keep"], g["ground"], g["cost"], r, params)
+    st = g["stats"]
+    assert st.n_dropped == r["dropped"]
+    assert st.n_nonfinite == r["nonfinite"]
+    assert st.n_points == len(points)
+    assert st.n_kept == int(g["keep"].sum())
+    N = grid.n_slices
+    np.testing.assert_array_equal(np.array(st.valid_cells[:N]),
+                                  (r["ground"] > -np.inf).reshape(N, -1).sum(1))
+    np.testing.assert_array_equal(np.array(st.trav_cells[:N]), g["mask"].reshape(N, -1).sum(1))
+    return g, r
+
+
+# ---------------------------------------------------------------- construction
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("stride", [3, 4])
+def test_build_random_cloud(seed, stride):
+    rng = np.random.default_rng(seed)
+    n = 50_003                                   # ragged: not a multiple of 4
+    pts = np.stack([rng.uniform(-0.5, 7.3, n), rng.uniform(-0.2, 5.1, n),
+                    rng.choice([0.0, 0.3, 1.2, 2.5], n) + rng.normal(0, 0.2, n)], 1).astype(np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 71, 49, 0.5, 6, 0.0, True)
+    ground, ceil, st = P.gpu_build(pts, grid, stride=stride)
+    eG, eC, og, dropped, bad = P.oracle.build(pts, P.oracle_grid(grid), True)
+    P.assert_equal_layers(ground, eG, "ground")
+    P.assert_equal_layers(ceil, eC, "ceiling")
+    assert st.n_dropped == dropped and st.n_nonfinite == 0
+    assert st.z_min == pts[:, 2].min() and st.z_max == pts[:, 2].max()
+
+
+def test_build_given_zmin_and_overflow_bin():
+    # explicit z_min and too few planes: points above the last plane only
+    # ever appear as ceilings
+    sc = scenes.building(5, 30_000, side_cells=60, floors=[0.0, 3.0], ceilings=[2.8, 5.8])
+    grid = _grid_of(sc, n_slices=5, zmin_from_data=False, z_min=-0.25)
+    ground, ceil, st = P.gpu_build(sc.points, grid)
+    eG, eC, _, _, _ = P.oracle.build(sc.points, P.oracle_grid(grid), False)
+    P.assert_equal_layers(ground, eG, "ground")
+    P.assert_equal_layers(ceil, eC, "ceiling")
+
+
+def test_build_nonfinite_and_offgrid_points():
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(0, 3, (1000, 3)).astype(np.float32)
+    pts[::17, 0] = np.nan
+    pts[5::23, 2] = np.inf
+    pts[7::31, 1] = -np.inf
+    pts[3::11, 0] = 50.0                         # far off the grid
+    pts[4::13, 2] = -0.0
+    grid = tct.Grid(0.0, 0.0, 0.1, 30, 30, 0.5, 7, 0.0, True)
+    ground, ceil, st = P.gpu_build(pts, grid)
+    eG, eC, _, dropped, bad = P.oracle.build(pts, P.oracle_grid(grid), True)
+    P.assert_equal_layers(ground, eG, "ground")
+    P.assert_equal_layers(ceil, eC, "ceiling")
+    assert st.n_nonfinite == bad > 0 and st.n_dropped == dropped > 0
+    assert st.status & tct.DEV_NONFINITE
+    assert not np.any((ground == 0) & np.signbit(ground))     # -0 is stored as +0
+
+
+def test_build_empty_cloud():
+    pts = np.zeros((0, 3), np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 20, 10, 0.5, 3, 0.0, False)
+    ground, ceil, st = P.gpu_build(pts, grid)
+    assert np.all(ground == -np.inf) and np.all(ceil == np.inf)
+
+
+# ------------------------------------------------------------------ evaluation
+
+def _evaluate_check(eG, eC, params, res=0.1):
+    N, H, W = eG.shape
+    grid = tct.Grid(0.0, 0.0, res, W, H, 0.5, N, 0.0, False)
+    g = P.gpu_evaluate(eG, eC, grid, params)
+    og = P.oracle.Grid(0.0, 0.0, res, W, H, 0.5, 0.0, N)
+    op = P.oracle_params(params)
+    cT, mask, frag, aux = P.oracle.evaluate(og, op, eG, eC, want_aux=True)
+    P.assert_costs(g["cost"], cT, frag)
+    P.assert_masks(g["mask"], mask, frag)
+    ok = np.broadcast_to((frag & 1) == 0, aux.shape)
+    ga = g["aux"].astype(np.float64)
+    fin = np.isfinite(aux)
+    assert np.array_equal(np.isfinite(ga), fin), "aux infinities differ"
+    err = np.abs(ga - aux)
+    lim = P.COST_RTOL * np.maximum(1.0, np.abs(aux))
+    assert np.all((err <= lim)[ok & fin]), "intermediate values out of tolerance"
+    keep_ref, robust = P.oracle.simplify(eG, cT, op["c_b"], frag)
+    P.assert_keep(g["keep"], eG, g["cost"], dict(keep=keep_ref, robust=robust), params)
+    return g, cT, frag
+
+
+@pytest.mark.parametrize("deg", [15.0, 25.0, 40.0])
+def test_evaluate_tilted_plane(deg):
+    t = math.tan(math.radians(deg))
+    H, W = 37, 45
+    j = np.arange(W)[None, :]
+    i = np.arange(H)[:, None]
+    eG = np.stack([((t * (j + 0.5) + 0.3 * t * (i + 0.5)) * 0.1).astype(np.float32)] * 2)
+    eC = np.full_like(eG, np.inf)
+    eC[1] = eG[1] + np.float32(0.55)
+    g, cT, frag = _evaluate_check(eG, eC, PARAMS_ROBOT)
+
+
+@pytest.mark.parametrize("params", [PARAMS_ROBOT, PARAMS_TABLE1,
+                                    dict(PARAMS_ROBOT, theta_p=1.0),
+                                    dict(PARAMS_ROBOT, patch_radius=0),
+                                    dict(PARAMS_ROBOT, patch_radius=4)])
+def test_evaluate_random_layers(params):
+    rng = np.random.default_rng(4)
+    N, H, W = 5, 83, 67                          # ragged against 16- and 32-cell tiles
+    base = (rng.normal(0, 0.04, (H, W)).cumsum(1) * 0.3).astype(np.float32)
+    eG = np.stack([base + 0.4 * k for k in range(N)]).astype(np.float32)
+    eG[rng.random(eG.shape) < 0.03] = -np.inf
+    eC = (eG + rng.uniform(0.3, 1.5, eG.shape)).astype(np.float32)
+    eC[rng.random(eG.shape) < 0.3] = np.inf
+    _evaluate_check(eG, eC, params)
+
+
+def test_evaluate_fine_resolution_radius_12():
+    # r_g = 0.05 m: D_inf = 6, D_sm = 7, a 25 x 25 window
+    rng = np.random.default_rng(12)
+    N, H, W = 3, 70, 90
+    eG = np.zeros((N, H, W), np.float32) + (rng.normal(0, 0.003, (N, H, W))).astype(np.float32)
+    eG[:, 30:33, 40:44] = 1.0                     # a block: barrier edges
+    eC = np.full((N, H, W), np.inf, np.float32)
+    _evaluate_check(eG, eC, PARAMS_ROBOT, res=0.05)
+
+
+def test_evaluate_nonmonotone_layers_simplification():
+    # layers that do not come from a build (ground not monotone in k)
+    rng = np.random.default_rng(2)
+    N, H, W = 6, 40, 40
+    eG = rng.choice([0.0, 0.5, 1.0], (N, 1, 1)).astype(np.float32) + np.zeros((N, H, W), np.float32)
+    eC = np.full((N, H, W), np.inf, np.float32)
+    eC[:, 10:20, 10:20] = eG[:, 10:20, 10:20] + rng.uniform(0.5, 0.7, (N, 1, 1)).astype(np.float32)
+    _evaluate_check(eG, eC, PARAMS_ROBOT)
+
+
+# --------------------------------------------------------- fused build + evaluate
+
+def test_two_storey_building_full():
+    sc = scenes.two_storey_building()
+    g, r = _full_check(sc.points, _grid_of(sc, n_slices=12), PARAMS_ROBOT)
+    assert r["robust"]
+    assert g["keep"].sum() >= 2
+
+
+@pytest.mark.parametrize("stride,misalign", [(4, False), (3, True)])
+def test_building_point_layouts(stride, misalign):
+    sc = scenes.building(8, 60_001, side_cells=90, floors=[0.0, 2.5], ceilings=[2.3, 4.9])
+    _full_check(sc.points, _grid_of(sc, n_slices=11), PARAMS_ROBOT, stride=stride,
+                misalign=misalign)
+
+
+def test_keep_ends_and_table1():
+    sc = scenes.building(10, 50_000, side_cells=70, floors=[0.0, 1.2, 2.9],
+                         ceilings=[1.0, 2.7, 4.0])
+    p = dict(PARAMS_TABLE1, flags=tct.KEEP_ENDS)
+    g, r = _full_check(sc.points, _grid_of(sc, n_slices=10), p)
+    assert g["keep"][0] == 1 and g["keep"][-1] == 1
+
+
+def test_single_slice_and_tiny_grid():
+    rng = np.random.default_rng(1)
+    pts = np.stack([rng.uniform(0, 0.5, 400), rng.uniform(0, 0.3, 400),
+                    rng.normal(0, 0.01, 400)], 1).astype(np.float32)
+    _full_check(pts, tct.Grid(0.0, 0.0, 0.1, 5, 3, 0.5, 1, 0.0, True), PARAMS_ROBOT)
+
+
+def test_parking_structure_full_size():
+    # the 5M-point, 1000 x 1000 x 40 workload in the launch configuration the
+    # benchmark times, every output compared with the oracle
+    sc = scenes.parking_structure()
+    g, r = _full_check(sc.points, _grid_of(sc), PARAMS_ROBOT)
+    assert r["robust"]
+
+
+def test_coverage_rule_rejected():
+    grid = tct.Grid(0.0, 0.0, 0.1, 8, 8, 0.6, 2, 0.0, False)
+    eG = np.zeros(grid.shape, np.float32)
+    with pytest.raises(tct.TctError, match="exceeds d_min"):
+        P.gpu_evaluate(eG, eG, grid, PARAMS_ROBOT)
+    g = P.gpu_evaluate(eG, np.full_like(eG, np.inf), grid, dict(PARAMS_ROBOT, flags=tct.ALLOW_COARSE))
+    assert g["cost"].shape == grid.shape
