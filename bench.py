@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["parking", "building"], default="parking")
+    ap.add_argument("--workload", choices=["parking", "parking-small", "building"],
+                    default="parking")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -47,6 +48,9 @@ def workload(name):
     from paper_2403_07631_gb300 import scenes
     if name == "parking":
         return scenes.parking_structure()
+    if name == "parking-small":
+        # the same structure on 60 x 60 m (600 x 600 x 40 outputs: 187 MB, above L2)
+        return scenes.parking_structure(n_points=1_800_000, side_cells=600)
     sc = scenes.two_storey_building()
     sc.n_slices = 12
     return sc

@@ -73,7 +73,7 @@ typedef struct tct_params {
     float d_min, d_ref;                /* Eq. 1: minimum and normal body height, m   */
     float theta_b, theta_s, theta_p;   /* Eq. 3-4: barrier, slope, step-safety       */
     float c_b;                         /* c^B, cost of a barrier                     */
-    float alpha_d, alpha_b, alpha_s;   /* Eq. 1, 4, 3 scaling factors                */
+    float alpha_d, alpha_b, alpha_s;   /* Eq. 1, 4, 3 scaling factors, >= 0          */
     float d_inf, d_sm;                 /* Eq. 6: inflation and safe-margin radii, m  */
     int32_t patch_radius;              /* R_p: p_s patch is (2R_p+1)^2 minus centre  */
     uint32_t flags;                    /* TCT_KEEP_ENDS | TCT_ALLOW_COARSE           */

@@ -14,7 +14,7 @@ namespace {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cnt, start, partial, zs, zkeys, upre, ubits, stats, total;
+    size_t cnt, start, partial, zs, scratch, long_count, long_cells, zkeys, upre, ubits, stats, total;
 };
 
 Layout layout(const tct_grid &g, int64_t n_points) {
@@ -26,6 +26,9 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     L.start = o; o = align_up(o + 4 * (m + 1));
     L.partial = o; o = align_up(o + 4 * (nb + 1));
     L.zs = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
+    L.scratch = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
+    L.long_count = o; o = align_up(o + 4);
+    L.long_cells = o; o = align_up(o + 4 * (n_points > 0 ? m : 0));
     L.zkeys = o; o = align_up(o + 4 * 2);
     L.upre = o; o = align_up(o + 4 * (TCT_MAX_SLICES + 1));
     L.ubits = o; o = align_up(o + 16 * (TCT_MAX_SLICES + 1));
@@ -82,6 +85,9 @@ Workspace carve(void *base, const tct_grid &g, int64_t n_points) {
     w.start = reinterpret_cast<int32_t *>(b + L.start);
     w.partial = reinterpret_cast<int32_t *>(b + L.partial);
     w.zs = reinterpret_cast<float *>(b + L.zs);
+    w.scratch = reinterpret_cast<float *>(b + L.scratch);
+    w.long_count = reinterpret_cast<int32_t *>(b + L.long_count);
+    w.long_cells = reinterpret_cast<int32_t *>(b + L.long_cells);
     w.zkeys = reinterpret_cast<int32_t *>(b + L.zkeys);
     w.upre = reinterpret_cast<int32_t *>(b + L.upre);
     w.ubits = reinterpret_cast<uint32_t *>(b + L.ubits);
@@ -97,6 +103,8 @@ int make_eval_consts(const tct_grid &g, const tct_params &p, EvalConsts *c) {
         if (!isfinite(v)) return TCT_ERR_INVALID_ARG;
     if (!(p.theta_s > 0.0f) || !(p.theta_b > 0.0f) || !(p.c_b > 0.0f) || p.d_inf < 0.0f)
         return TCT_ERR_INVALID_ARG;
+    // the scaling factors are non-negative (Table I); -0 is folded to +0
+    if (p.alpha_d < 0.0f || p.alpha_b < 0.0f || p.alpha_s < 0.0f) return TCT_ERR_INVALID_ARG;
     if (p.patch_radius < 0) return TCT_ERR_INVALID_ARG;
     if (p.patch_radius > TCT_MAX_PATCH_RADIUS) return TCT_ERR_UNSUPPORTED;
     if (g.d_s > p.d_min && !(p.flags & TCT_ALLOW_COARSE)) return TCT_ERR_COVERAGE;
@@ -106,9 +114,9 @@ int make_eval_consts(const tct_grid &g, const tct_params &p, EvalConsts *c) {
     c->theta_b = p.theta_b;
     c->theta_s = p.theta_s;
     c->c_b = p.c_b;
-    c->alpha_d = p.alpha_d;
-    c->alpha_b = p.alpha_b;
-    c->alpha_s = p.alpha_s;
+    c->alpha_d = p.alpha_d + 0.0f;
+    c->alpha_b = p.alpha_b + 0.0f;
+    c->alpha_s = p.alpha_s + 0.0f;
     c->inv2r = (float)(1.0 / (2.0 * (double)g.res));
     c->inv_ts = (float)(1.0 / (double)p.theta_s);
     c->inv_tb = (float)(1.0 / (double)p.theta_b);

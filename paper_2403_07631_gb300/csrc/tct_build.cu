@@ -359,17 +359,88 @@ k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restric
     if (blockIdx.x == 0 && threadIdx.x == 0) start[m] = partial[nb];
 }
 
-// Sort each cell's segment ascending (insertion sort; segments are short).
+// Sort each cell's segment ascending.  Segments of up to 16 heights are
+// sorted in registers by a bitonic network (padded with +inf); longer ones
+// are queued for k_sort_long.
+template <int L>
+__device__ __forceinline__ void bitonic_sort(float (&v)[L]) {
+#pragma unroll
+    for (int size = 2; size <= L; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                const int jx = i ^ stride;
+                if (jx > i) {
+                    const bool up = (i & size) == 0;
+                    const float a = v[i], b = v[jx];
+                    const float lo = fminf(a, b), hi = fmaxf(a, b);
+                    v[i] = up ? lo : hi;
+                    v[jx] = up ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void sort_segment(float *__restrict__ zs, int32_t s, int32_t n) {
+    float v[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = i < n ? zs[s + i] : INFINITY;
+    bitonic_sort<L>(v);
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+        if (i < n) zs[s + i] = v[i];
+}
+
 __global__ void __launch_bounds__(kThreads)
-k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ zs) {
+k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ zs,
+             int32_t *__restrict__ long_count, int32_t *__restrict__ long_cells) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
-    const int32_t s = start[c], e = start[c + 1];
-    for (int32_t i = s + 1; i < e; ++i) {
-        const float v = zs[i];
-        int32_t j = i - 1;
-        while (j >= s && zs[j] > v) { zs[j + 1] = zs[j]; --j; }
-        zs[j + 1] = v;
+    const int32_t s = start[c], n = start[c + 1] - s;
+    if (n <= 1) return;
+    if (n <= 4) sort_segment<4>(zs, s, n);
+    else if (n <= 8) sort_segment<8>(zs, s, n);
+    else if (n <= 16) sort_segment<16>(zs, s, n);
+    else long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
+}
+
+// One warp per long segment: each height's final position is its rank (the
+// count of smaller heights, ties broken by index).  The segment is staged in
+// shared memory when it fits, else read from a copy in global scratch.
+constexpr int kLongStage = 1024;
+
+__global__ void __launch_bounds__(kThreads)
+k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
+            float *__restrict__ scratch, const int32_t *__restrict__ long_count,
+            const int32_t *__restrict__ long_cells) {
+    __shared__ float stage[kThreads / 32][kLongStage];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int total = *long_count;
+    for (int t = blockIdx.x * (kThreads / 32) + wib; t < total; t += gridDim.x * (kThreads / 32)) {
+        const int32_t c = long_cells[t];
+        const int32_t s = start[c], n = start[c + 1] - s;
+        const float *src;
+        if (n <= kLongStage) {
+            for (int i = lane; i < n; i += 32) stage[wib][i] = zs[s + i];
+            src = stage[wib];
+        } else {
+            for (int i = lane; i < n; i += 32) scratch[s + i] = zs[s + i];
+            src = scratch + s;
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const float z = src[i];
+            int32_t rank = 0;
+            for (int j = 0; j < n; ++j) {
+                const float y = src[j];
+                rank += (y < z) || (y == z && j < i);
+            }
+            zs[s + rank] = z;
+        }
+        __syncwarp();
     }
 }
 
@@ -461,8 +532,12 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     if (n > 0)
         k_scatter<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                    ws.start, ws.zs);
-    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(ws.start, m, ws.zs);
-    count_launches(n > 0 ? 8 : 6);
+    cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
+    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        ws.start, m, ws.zs, ws.long_count, ws.long_cells);
+    k_sort_long<<<grid_blocks(m, 64 * kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                                    ws.long_count, ws.long_cells);
+    count_launches(n > 0 ? 9 : 7);
     return cudaGetLastError();
 }
 

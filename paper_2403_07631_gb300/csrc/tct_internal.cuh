@@ -35,6 +35,9 @@ struct Workspace {
     int32_t *start;     // [HW+1] exclusive prefix of cnt
     int32_t *partial;   // [n_scan_blocks + 1]
     float *zs;          // [P]    point heights grouped by cell, sorted per cell
+    float *scratch;     // [P]    copy of very long segments while they are sorted
+    int32_t *long_count;  // [1]  cells whose segment needs the warp sort
+    int32_t *long_cells;  // [HW] their indices
     int32_t *zkeys;     // [2]    ordered-int min / max z of the finite points
     int32_t *upre;      // [128]  per slice: bits [0, upre) of the uniqueness row set
     uint32_t *ubits;    // [128][4] per slice: further uniqueness bits
@@ -64,6 +67,23 @@ int make_eval_consts(const tct_grid &g, const tct_params &p, EvalConsts *c);
 // Host-side count of kernel launches (tct_launch_count).
 void count_launches(int n);
 
+// Arguments of the slice-stack kernels (tct_stack.cu, tct_stack_inc.cu).
+struct StackArgs {
+    int32_t W, H, N;
+    float d_s, z_min;
+    int32_t zmin_from_data;
+    const int32_t *zkeys;        // ordered-int z bounds from the count pass
+    const int32_t *start;        // per-cell segments (build path)
+    const float *zs;
+    const float *gin, *cin;      // given layers (evaluate path)
+    float *ground, *ceil, *cost, *aux;
+    uint8_t *mask;
+    int32_t *upre;
+    uint32_t *ubits;
+    tct_stats *stats;
+    EvalConsts c;
+};
+
 // launchers (tct_build.cu)
 cudaError_t launch_bounds(const float *xyz, int64_t n, int stride, float *out6,
                           tct_stats *stats, cudaStream_t s);
@@ -77,6 +97,9 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
                          const int32_t *zkeys, const float *gin, const float *cin,
                          float *ground, float *ceil, float *cost, uint8_t *mask, float *aux,
                          int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s);
+// The incremental kernel for the build path; returns cudaErrorNotSupported
+// when no instance matches the window radii (the caller then falls back).
+cudaError_t launch_stack_inc(const StackArgs &a, cudaStream_t s);
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits,
                          uint32_t flags, uint8_t *keep, tct_stats *stats, cudaStream_t s);
 

@@ -26,21 +26,7 @@
 namespace tct {
 namespace {
 
-struct StackArgs {
-    int32_t W, H, N;
-    float d_s, z_min;
-    int32_t zmin_from_data;
-    const int32_t *zkeys;        // ordered-int z bounds from the count pass
-    const int32_t *start;        // per-cell segments (build path)
-    const float *zs;
-    const float *gin, *cin;      // given layers (evaluate path)
-    float *ground, *ceil, *cost, *aux;
-    uint8_t *mask;
-    int32_t *upre;
-    uint32_t *ubits;
-    tct_stats *stats;
-    EvalConsts c;
-};
+
 
 struct Geo {
     int RK, RP, HE, EW, EH, GW, GH, CW, CH;
@@ -433,7 +419,11 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.c = c;
     k_stack_init<<<1, 128, 0, s>>>(upre, ubits);
     count_launches(1);
-    if (lists) return pick_tile<true, false>(a, s);
+    if (lists) {
+        const cudaError_t e = launch_stack_inc(a, s);
+        if (e != cudaErrorNotSupported) return e;
+        return pick_tile<true, false>(a, s);
+    }
     if (aux) return pick_tile<false, true>(a, s);
     return pick_tile<false, false>(a, s);
 }

@@ -282,7 +282,8 @@ def parking_structure(seed: int = 2, n_points: int = 5_000_000, side_cells: int 
         return _rand_rect_h(rng, m, 0.0, 0.0, L, L, 16.0, sigma, keep=floor_keep(16.0))
 
     pts = _finish(rng, parts, n_points, topup)
-    return Scene("parking structure 5M pts, 1000x1000 @0.1 m, 40 slices", pts, 0.0, 0.0, res,
+    name = f"parking structure {n_points / 1e6:g}M pts, {side_cells}x{side_cells} @{res:g} m, 40 slices"
+    return Scene(name, pts, 0.0, 0.0, res,
                  side_cells, side_cells, 0.5, 40,
                  dict(seed=seed, levels=levels, n_pillars=n_pillars, n_beams=n_beams))
 

@@ -41,6 +41,7 @@ def _full_check(points, grid, params, stride=3, misalign=False):
     P.assert_masks(g["mask"], r["mask"], r["fragile"])
     P.assert_keep(g["keep"], g["ground"], g["cost"], r, params)
     st = g["stats"]
+    assert st.status == 0 or st.n_nonfinite > 0
     assert st.n_dropped == r["dropped"]
     assert st.n_nonfinite == r["nonfinite"]
     assert st.n_points == len(points)
@@ -222,3 +223,28 @@ def test_coverage_rule_rejected():
         P.gpu_evaluate(eG, eG, grid, PARAMS_ROBOT)
     g = P.gpu_evaluate(eG, np.full_like(eG, np.inf), grid, dict(PARAMS_ROBOT, flags=tct.ALLOW_COARSE))
     assert g["cost"].shape == grid.shape
+
+
+def test_fine_resolution_build_radius_12():
+    # r_g = 0.05 m: the 25 x 25 inflation window of the build path
+    sc = scenes.building(14, 120_000, side_cells=150, res=0.05, floors=[0.0, 1.1, 2.3],
+                         ceilings=[0.9, 2.0, 3.6])
+    _full_check(sc.points, _grid_of(sc, n_slices=9), PARAMS_ROBOT)
+
+
+def test_generic_window_fallback():
+    # a patch radius without a specialised instance takes the generic kernel
+    sc = scenes.building(15, 40_000, side_cells=70, floors=[0.0, 2.0], ceilings=[1.8, 3.9])
+    _full_check(sc.points, _grid_of(sc, n_slices=9), dict(PARAMS_ROBOT, patch_radius=3))
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_many_slices_dense_changes(seed):
+    # noisy multi-level clutter: grounds and ceilings change in most slices
+    rng = np.random.default_rng(seed)
+    n = 200_000
+    xy = rng.uniform(0, 13.0, (n, 2))
+    z = rng.choice(np.arange(0, 12, 0.7), n) + rng.normal(0, 0.08, n)
+    pts = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 130, 130, 0.25, 48, 0.0, True)
+    _full_check(pts, grid, dict(PARAMS_ROBOT, d_min=0.3, d_ref=0.45))
