@@ -407,9 +407,11 @@ k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ z
     else long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
 }
 
-// One warp per long segment: each height's final position is its rank (the
-// count of smaller heights, ties broken by index).  The segment is staged in
-// shared memory when it fits, else read from a copy in global scratch.
+// One warp per long segment.  Up to kLongStage heights are sorted by a
+// bitonic network in the warp's shared-memory buffer (padded with +inf);
+// longer segments, which no sensible cloud has, fall back to placing every
+// height at its rank (smaller heights, ties broken by index) from a copy in
+// global scratch.
 constexpr int kLongStage = 1024;
 
 __global__ void __launch_bounds__(kThreads)
@@ -419,28 +421,45 @@ k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
     __shared__ float stage[kThreads / 32][kLongStage];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int total = *long_count;
+    float *buf = stage[wib];
     for (int t = blockIdx.x * (kThreads / 32) + wib; t < total; t += gridDim.x * (kThreads / 32)) {
         const int32_t c = long_cells[t];
         const int32_t s = start[c], n = start[c + 1] - s;
-        const float *src;
         if (n <= kLongStage) {
-            for (int i = lane; i < n; i += 32) stage[wib][i] = zs[s + i];
-            src = stage[wib];
+            int L = 32;
+            while (L < n) L <<= 1;
+            for (int i = lane; i < L; i += 32) buf[i] = i < n ? zs[s + i] : INFINITY;
+            __syncwarp();
+            for (int size = 2; size <= L; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = lane; i < L; i += 32) {
+                        const int jx = i ^ stride;
+                        if (jx > i) {
+                            const float x = buf[i], y = buf[jx];
+                            const bool up = (i & size) == 0;
+                            if ((x > y) == up) { buf[i] = y; buf[jx] = x; }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int i = lane; i < n; i += 32) zs[s + i] = buf[i];
+            __syncwarp();
         } else {
             for (int i = lane; i < n; i += 32) scratch[s + i] = zs[s + i];
-            src = scratch + s;
-        }
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const float z = src[i];
-            int32_t rank = 0;
-            for (int j = 0; j < n; ++j) {
-                const float y = src[j];
-                rank += (y < z) || (y == z && j < i);
+            __syncwarp();
+            const float *src = scratch + s;
+            for (int i = lane; i < n; i += 32) {
+                const float z = src[i];
+                int32_t rank = 0;
+                for (int j = 0; j < n; ++j) {
+                    const float y = src[j];
+                    rank += (y < z) || (y == z && j < i);
+                }
+                zs[s + rank] = z;
             }
-            zs[s + rank] = z;
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 

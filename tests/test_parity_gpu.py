@@ -248,3 +248,19 @@ def test_many_slices_dense_changes(seed):
     pts = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
     grid = tct.Grid(0.0, 0.0, 0.1, 130, 130, 0.25, 48, 0.0, True)
     _full_check(pts, grid, dict(PARAMS_ROBOT, d_min=0.3, d_ref=0.45))
+
+
+def test_long_cell_segments():
+    # cells holding 20, 300 and 3000 points (a vertical scan line): the
+    # register networks, the warp bitonic sort and the rank sort all run
+    rng = np.random.default_rng(31)
+    base = np.stack([rng.uniform(0, 4.0, 30_000), rng.uniform(0, 4.0, 30_000),
+                     rng.normal(0, 0.01, 30_000)], 1)
+    cols = []
+    for (x, y, m) in ((1.05, 1.05, 20), (2.05, 1.55, 300), (3.05, 2.55, 3000)):
+        z = rng.uniform(0.0, 6.0, m)
+        z[: m // 10] = np.round(z[: m // 10], 1)          # repeated heights
+        cols.append(np.stack([np.full(m, x), np.full(m, y), z], 1))
+    pts = np.concatenate([base] + cols).astype(np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 40, 40, 0.5, 13, 0.0, True)
+    _full_check(pts, grid, PARAMS_ROBOT)
