@@ -138,6 +138,28 @@ def measured_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def stack_traffic():
+    """DRAM bytes per launch of the stack kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_stack_inc_parking.txt")
+    src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cu")
+    try:
+        rec = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        if rec.get("kernel_source_sha256_16") != digest:
+            return None
+        return int(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
@@ -286,14 +308,7 @@ def main():
     path_gbs = algorithmic_bytes(P, N, H, W) / (ms * 1e-3) / 1e9
     sb = stack_bytes(P, N, H, W)
     stack_gbs = sb / (stack_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "stack_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                traffic = json.load(f).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = stack_traffic()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -303,7 +318,7 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
                           "peak_source": peak_src},
-        "roofline": {"kernel": "k_stack (per-tile slice stack)", "bound": "hbm",
+        "roofline": {"kernel": "k_stack_inc (per-tile incremental slice stack)", "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
                      "traffic": traffic, "algorithmic_bytes": sb, "ms": stack_ms,
                      "peak_source": peak_src},
