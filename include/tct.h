@@ -170,6 +170,34 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
                        float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
                        uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
 
+/* ---- no-allocation variant ---------------------------------------------- */
+
+/* Scratch compiled into the library for tct_build_evaluate_noalloc, per device. */
+#define TCT_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * tct_build_evaluate without a workspace argument, for callers that cannot
+ * allocate device memory when they need the tomogram (a control loop whose
+ * memory is reserved at start-up, a plug-in whose host owns the allocator).
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * The scratch is a fixed array of TCT_NOALLOC_SCRATCH_BYTES inside the
+ * library, held by every GPU that loads the library until the process exits.
+ * Returns TCT_ERR_WORKSPACE_TOO_SMALL when tct_workspace_bytes(grid, n,
+ * params) exceeds it (about 12 bytes per cell plus 8 per point: the 200 x 200,
+ * 200k-point building fits, the 1000 x 1000, 5M-point parking structure does
+ * not), and otherwise exactly what tct_build_evaluate returns.  It calls no
+ * allocation routine.  The first call on a device looks up the array's device
+ * address (with that device current) and should come before any stream
+ * capture.  Every call uses the same array and leaves its contents behind;
+ * the call clears what it needs zeroed itself.  Calls that overlap on the GPU
+ * race on the array: serialise them.
+ */
+int tct_build_evaluate_noalloc(const float *d_xyz, int64_t n, int32_t stride,
+                               const tct_grid *grid, const tct_params *params, float *d_ground,
+                               float *d_ceil, float *d_cost, uint8_t *d_mask, uint8_t *d_keep,
+                               tct_stats *d_stats, tct_stream stream);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /*

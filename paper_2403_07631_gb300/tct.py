@@ -23,6 +23,7 @@ GRID_ZMIN_FROM_DATA = 1
 KEEP_ENDS = 1
 ALLOW_COARSE = 2
 DEV_NONFINITE = 1
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class TctGrid(ctypes.Structure):
@@ -68,6 +69,10 @@ _SIGNATURES = {
     "tct_build_evaluate": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(TctGrid), ctypes.POINTER(TctParams), _P,
                                           ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P]),
+    "tct_build_evaluate_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32,
+                                                  ctypes.POINTER(TctGrid),
+                                                  ctypes.POINTER(TctParams), _P, _P, _P, _P, _P,
+                                                  _P, _P]),
     "tct_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
@@ -229,6 +234,21 @@ def tct_build_evaluate(xyz: torch.Tensor, grid: Grid, params: dict, ws: torch.Te
                                      ctypes.byref(cp), _ptr(ws), ws.numel() * ws.element_size(),
                                      _ptr(ground), _ptr(ceil), _ptr(cost), _ptr(mask), _ptr(keep),
                                      _ptr(stats), _stream()))
+
+
+def tct_build_evaluate_noalloc(xyz: torch.Tensor, grid: Grid, params: dict, ground: torch.Tensor,
+                               ceil: torch.Tensor, cost: torch.Tensor, mask: torch.Tensor,
+                               keep: torch.Tensor, stats: torch.Tensor | None = None):
+    """tct_build_evaluate with the library's fixed scratch instead of a workspace, for
+    callers that cannot allocate device memory; maps needing more than
+    NOALLOC_SCRATCH_BYTES of scratch are refused."""
+    n, stride = _points(xyz)
+    cp = _params_c(params)
+    _check("tct_build_evaluate_noalloc",
+           load().tct_build_evaluate_noalloc(_ptr(xyz), n, stride, ctypes.byref(grid.c()),
+                                             ctypes.byref(cp), _ptr(ground), _ptr(ceil),
+                                             _ptr(cost), _ptr(mask), _ptr(keep), _ptr(stats),
+                                             _stream()))
 
 
 # --------------------------------------------------------------- helpers
