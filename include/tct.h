@@ -3,7 +3,7 @@
  *
  * Method: Yang et al., "Efficient Global Navigational Planning in 3D
  * Structures based on Point Cloud Tomography", arXiv 2403.07631.
- *   Sec. III-A / Alg. 1 lines 1-6   tomogram construction (tct_build)
+ *   Sec. III-A / Alg. 1 (construction)  tomogram construction (tct_build)
  *   Sec. III-B / Eq. 1-6            scene evaluation (tct_evaluate)
  *   Sec. III-C / Eq. 7-9            slice simplification (tct_evaluate)
  *   Sec. III-E / Eq. 10             cost and elevation queries (tct_sample_cost)
@@ -53,7 +53,7 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 #define TCT_MAX_POINTS 2000000000LL    /* points per call                    */
 
 /* ---- geometry (Sec. III-A) ---------------------------------------------- */
-#define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (Alg. 1 line 1) */
+#define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (first step of Alg. 1) */
 
 typedef struct tct_grid {
     float x0, y0;      /* world position of the corner of cell (0,0), m       */
@@ -132,7 +132,7 @@ int tct_bounds(const float *d_xyz, int64_t n, int32_t stride, float *d_out6,
                tct_stats *d_stats, tct_stream stream);
 
 /*
- * Sec. III-A, Alg. 1 lines 1-6: ground and ceiling layers.  For every slice
+ * Sec. III-A and the construction part of Alg. 1: ground and ceiling layers.  For every slice
  * k and cell: ground = highest point z <= h_k in the cell, ceiling = lowest
  * point z > h_k, with h_k = fl32(z_min + (k+1) d_s); a point's cell is
  * (floor(fl32(fl32(y-y0)/res)), floor(fl32(fl32(x-x0)/res))).  Points off the

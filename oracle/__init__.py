@@ -10,7 +10,7 @@ out.  Every function cites the passage of the paper it restates:
 
 - ``derive_grid``      Sec. III-A (planes d_s apart, the first d_s above the
                        lowest point, the last above the highest point)
-- ``build``            Alg. 1 lines 1-6 and Sec. III-A (ground = highest point
+- ``build``            Alg. 1 (construction) and Sec. III-A (ground = highest point
                        of the lower group, ceiling = lowest of the upper group)
 - ``kernel``           Eq. 6 (inflation weights)
 - ``evaluate``         Sec. III-B, Eq. 1-6 (interval, gradient, terrain and
@@ -163,7 +163,7 @@ def derive_grid(xyz: np.ndarray, res: float, d_s: float) -> Grid:
 
 
 def build(xyz: np.ndarray, g: Grid, zmin_from_data: bool = True):
-    """Alg. 1 lines 1-6 by brute force.  Returns (eG, eC, grid, n_dropped, n_nonfinite);
+    """The construction of Alg. 1 by brute force.  Returns (eG, eC, grid, n_dropped, n_nonfinite);
     eG/eC are [N,H,W] float32 with -inf/+inf for invalid cells."""
     xyz, stride = _points(xyz)
     cg = g.c()

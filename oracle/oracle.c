@@ -172,9 +172,9 @@ int oracle_derive_grid(const float *xyz, int64_t n, int32_t stride, float res,
 }
 
 /*
- * Algorithm 1, lines 1-6, brute force: every slice scans every point.
+ * The construction part of Algorithm 1, brute force: every slice scans every point.
  * eG, eC: [N][H][W] float32.  When zmin_from_data is set, g->z_min is
- * replaced by the lowest finite z of the whole cloud (Alg. 1 line 1).
+ * replaced by the lowest finite z of the whole cloud (the first step of Alg. 1).
  */
 int oracle_build(const float *xyz, int64_t n, int32_t stride, oracle_grid *g,
                  int32_t zmin_from_data, float *eG, float *eC, int64_t *n_dropped,

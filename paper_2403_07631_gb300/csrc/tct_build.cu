@@ -1,4 +1,4 @@
-// tct_build.cu -- tomogram construction kernels (Sec. III-A, Alg. 1 lines 1-6).
+// tct_build.cu -- tomogram construction kernels (Sec. III-A, the construction part of Alg. 1).
 //
 // The cloud is partitioned by cell with a counting sort:
 //   count    one pass over the points: rasterise, per-cell histogram with

@@ -1,4 +1,4 @@
-"""Pins of the oracle's tomogram construction (Sec. III-A, Alg. 1 lines 1-6).
+"""Pins of the oracle's tomogram construction (Sec. III-A, the construction part of Alg. 1).
 
 Nothing here re-types the oracle's loops: expected values are enumerated by
 hand, follow from closed forms, are checked as invariants, or come from an

@@ -69,7 +69,7 @@ def _assert_coverage(eG, cT, keep, c_b=50.0):
 def test_identical_slices_keep_one(oracle_mod):
     # Two identical floors in slices 0 and 1 and an upper floor in slice 2.
     # Testing every slice against its original neighbours (the literal reading
-    # of Alg. 1 lines 9-11) would drop both floor slices; the sequential chain
+    # of the removal loop of Alg. 1) would drop both floor slices; the sequential chain
     # of Sec. III-C keeps exactly one of them.
     N, H, W = 3, 6, 6
     eG = np.zeros((N, H, W), np.float32)
