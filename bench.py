@@ -49,8 +49,10 @@ def workload(name):
     if name == "parking":
         return scenes.parking_structure()
     if name == "parking-small":
-        # the same structure on 60 x 60 m (600 x 600 x 40 outputs: 187 MB, above L2)
-        return scenes.parking_structure(n_points=1_800_000, side_cells=600)
+        # the same structure on 60 x 60 m, pillars and beams scaled with the area
+        # (600 x 600 x 40 outputs: 187 MB, above L2)
+        return scenes.parking_structure(n_points=1_800_000, side_cells=600, n_pillars=144,
+                                        n_beams=108)
     sc = scenes.two_storey_building()
     sc.n_slices = 12
     return sc

@@ -2,7 +2,7 @@
 //
 // The cloud is partitioned by cell with a counting sort:
 //   count    one pass over the points: rasterise, per-cell histogram with
-//            warp-aggregated atomics, bounds of z (ordered-int atomics),
+//            L2 atomics, bounds of z (block-reduced ordered-int atomics),
 //            dropped / non-finite counts;
 //   scan     exclusive prefix of the histogram (three small kernels);
 //   scatter  second pass over the points: each z lands in its cell's segment;
@@ -116,19 +116,14 @@ __device__ void flush_tally(PointTally t, int32_t *zkeys, tct_stats *stats, bool
 // Warp-aggregated update of a per-cell counter: lanes of the warp that hit the
 // same cell are served by one atomic; returns this lane's slot (0-based rank
 // among the lanes of its group, plus the counter value the group saw).
+// Per-cell counter update; returns this point's slot.  (A warp-aggregated
+// form with __match_any_sync was measured slower: in stratified and
+// spatially sorted clouds the 32 points of a warp fall in 32 distinct cells,
+// so the match only adds work.)
 template <bool kSubtract>
-__device__ __forceinline__ int32_t aggregated_atomic(int32_t *ctr, int cell) {
-    const unsigned active = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int key = cell >= 0 ? cell : -1 - lane;        // off-grid lanes stay alone
-    const unsigned group = __match_any_sync(active, key);
-    const int leader = __ffs(group) - 1;
-    const int rank = __popc(group & ((1u << lane) - 1u));
-    int32_t base = 0;
-    if (cell >= 0 && lane == leader)
-        base = kSubtract ? atomicSub(&ctr[cell], __popc(group)) : atomicAdd(&ctr[cell], __popc(group));
-    base = __shfl_sync(active, base, leader);
-    return kSubtract ? base - 1 - rank : base + rank;
+__device__ __forceinline__ int32_t cell_slot(int32_t *ctr, int cell) {
+    if (cell < 0) return -1;
+    return kSubtract ? atomicSub(&ctr[cell], 1) - 1 : atomicAdd(&ctr[cell], 1);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -205,7 +200,7 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
             cell = cell_of(g, x, y);
             if (cell < 0) ++t.dropped;
         }
-        aggregated_atomic<false>(cnt, cell);
+        cell_slot<false>(cnt, cell);
     };
     // the loop bound is warp-uniform so that every lane joins each match
     for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
@@ -216,7 +211,7 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (ok) visit(p[q][0], p[q][1], p[q][2]);
-            else aggregated_atomic<false>(cnt, -1);
+            else cell_slot<false>(cnt, -1);
         }
     }
     for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
@@ -226,7 +221,7 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
             load1(xyz, stride, i, p);
             visit(p[0], p[1], p[2]);
         } else {
-            aggregated_atomic<false>(cnt, -1);
+            cell_slot<false>(cnt, -1);
         }
     }
     flush_tally(t, zkeys, stats, true);
@@ -242,7 +237,7 @@ k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDe
     const int64_t ngroups = vec ? n / 4 : 0;
     auto visit = [&](float x, float y, float z) {
         const int cell = finite3(x, y, z) ? cell_of(g, x, y) : -1;
-        const int32_t slot = aggregated_atomic<true>(cnt, cell);
+        const int32_t slot = cell_slot<true>(cnt, cell);
         if (cell >= 0) zs[start[cell] + slot] = fold_zero(z);
     };
     for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
@@ -253,7 +248,7 @@ k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDe
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (ok) visit(p[q][0], p[q][1], p[q][2]);
-            else aggregated_atomic<true>(cnt, -1);
+            else cell_slot<true>(cnt, -1);
         }
     }
     for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
@@ -263,7 +258,7 @@ k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDe
             load1(xyz, stride, i, p);
             visit(p[0], p[1], p[2]);
         } else {
-            aggregated_atomic<true>(cnt, -1);
+            cell_slot<true>(cnt, -1);
         }
     }
 }
@@ -554,7 +549,7 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
     k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<grid_blocks(m, 64 * kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+    k_sort_long<<<grid_blocks(m, kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
                                                                     ws.long_count, ws.long_cells);
     count_launches(n > 0 ? 9 : 7);
     return cudaGetLastError();

@@ -326,12 +326,22 @@ k_stack(const __grid_constant__ StackArgs a) {
 // The sequential chain of Sec. III-C over the uniqueness matrix.
 __global__ void k_chain(int n_slices, const int32_t *upre, const uint32_t *ubits, uint32_t flags,
                         uint8_t *keep, tct_stats *stats) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ int32_t s_pre[TCT_MAX_SLICES + 1];
+    __shared__ uint32_t s_bits[4 * (TCT_MAX_SLICES + 1)];
+    for (int k = threadIdx.x; k < n_slices; k += blockDim.x) {
+        s_pre[k] = upre[k];
+        s_bits[4 * k] = ubits[4 * k];
+        s_bits[4 * k + 1] = ubits[4 * k + 1];
+        s_bits[4 * k + 2] = ubits[4 * k + 2];
+        s_bits[4 * k + 3] = ubits[4 * k + 3];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     int p = -1;
     int kept = 0;
     for (int k = 0; k < n_slices; ++k) {
         const int row = p + 1;
-        bool u = row < upre[k] || ((ubits[4 * k + (row >> 5)] >> (row & 31)) & 1u);
+        bool u = row < s_pre[k] || ((s_bits[4 * k + (row >> 5)] >> (row & 31)) & 1u);
         if ((flags & TCT_KEEP_ENDS) && (k == 0 || k == n_slices - 1)) u = true;
         keep[k] = u ? 1 : 0;
         if (u) { p = k; ++kept; }
@@ -430,7 +440,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
 
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits, uint32_t flags,
                          uint8_t *keep, tct_stats *stats, cudaStream_t s) {
-    k_chain<<<1, 32, 0, s>>>(n_slices, upre, ubits, flags, keep, stats);
+    k_chain<<<1, 128, 0, s>>>(n_slices, upre, ubits, flags, keep, stats);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -261,13 +261,14 @@ def parking_structure(seed: int = 2, n_points: int = 5_000_000, side_cells: int 
     del n_ramp_cells
     # slab undersides of the upper levels
     for lv in levels[1:]:
-        parts.append(_rand_rect_h(rng, 100_000, 0.0, 0.0, L, L, lv - 0.3, sigma, keep=floor_keep(lv)))
+        parts.append(_rand_rect_h(rng, side_cells * side_cells // 10, 0.0, 0.0, L, L, lv - 0.3, sigma,
+                                  keep=floor_keep(lv)))
     # pillars through all levels
-    per = rng.multinomial(350_000, np.ones(len(pill)) / len(pill))
+    per = rng.multinomial(875 * len(pill), np.ones(len(pill)) / len(pill))
     for (px, py, hx, hy), m in zip(pill, per):
         parts.append(_rand_box_sides(rng, m, px, py, hx, hy, 0.0, 16.0, sigma))
     # overhanging beams: undersides 1.6-2.4 m above a floor, 0.3 m wide, 4-12 m long
-    per = rng.multinomial(150_000, np.ones(n_beams) / n_beams)
+    per = rng.multinomial(500 * n_beams, np.ones(n_beams) / n_beams)
     for m in per:
         lv = levels[rng.integers(0, 4)]
         z = lv + rng.uniform(1.6, 2.4)
