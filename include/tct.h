@@ -52,6 +52,13 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 #define TCT_MAX_PATCH_RADIUS 4         /* p_s patch radius in cells          */
 #define TCT_MAX_POINTS 2000000000LL    /* points per call                    */
 
+#define TCT_MAX_BATCH 64               /* maps per batched call              */
+
+/* tile shapes of the slice-stack kernel (tct_tuning.tile) */
+#define TCT_TILE_AUTO 0                /* 64 x 64 unless that leaves SMs idle */
+#define TCT_TILE_64 1                  /* 64 x 64 cells, 512 threads          */
+#define TCT_TILE_32 2                  /* 32 x 32 cells, 128 threads          */
+
 /* ---- geometry (Sec. III-A) ---------------------------------------------- */
 #define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (first step of Alg. 1) */
 
@@ -169,6 +176,60 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
                        const tct_params *params, void *d_ws, size_t ws_bytes,
                        float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
                        uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
+
+/* ---- batches of maps ---------------------------------------------------- */
+
+/* One map of a batch: its cloud, its grid and its own output buffers. */
+typedef struct tct_map {
+    const float *d_xyz;      /* n points, `stride` floats apart (3 or 4)          */
+    int64_t n;
+    int32_t stride;
+    int32_t reserved;        /* 0                                                 */
+    tct_grid grid;
+    float *d_ground, *d_ceil, *d_cost;   /* [N][H][W] float32                    */
+    uint8_t *d_mask;                     /* [N][H][W]                            */
+    uint8_t *d_keep;                     /* [N]                                  */
+    tct_stats *d_stats;                  /* may be NULL                          */
+} tct_map;
+
+/* Launch choices for a batch, from tct_autotune_batched or by hand. */
+typedef struct tct_tuning {
+    int32_t tile;              /* TCT_TILE_*                                      */
+    int32_t ctas_per_sm;       /* persistent CTAs per SM; 0 = as many as fit      */
+    int32_t points_per_block;  /* points per block of the two point passes, % 4   */
+    int32_t reserved;
+} tct_tuning;
+
+/* Workspace of tct_build_evaluate_batched; 0 for an invalid batch. */
+size_t tct_workspace_bytes_batched(const tct_map *h_maps, int32_t n_maps,
+                                   const tct_params *params);
+
+/*
+ * tct_build_evaluate on up to TCT_MAX_BATCH independent maps at once (the
+ * batching extension of the method: many maps of uneven size, one set of
+ * launches).  h_maps is a host array; the pointers inside it are device
+ * pointers.  The point passes run over all clouds together, the per-tile
+ * slice stack is one persistent launch that takes (map, tile) items from a
+ * queue, largest maps first, and one launch runs every map's chain.  The
+ * launch sequence does not depend on the data, so it can be captured into a
+ * CUDA graph and replayed.  All maps share r_g and the robot parameters;
+ * window radii without a specialised kernel give TCT_ERR_UNSUPPORTED.
+ * tuning may be NULL (defaults).  Each map's outputs are those of
+ * tct_build_evaluate on that map alone.
+ */
+int tct_build_evaluate_batched(const tct_map *h_maps, int32_t n_maps, const tct_params *params,
+                               const tct_tuning *tuning, void *d_ws, size_t ws_bytes,
+                               tct_stream stream);
+
+/*
+ * Times tct_build_evaluate_batched on this batch for each candidate tuning
+ * (tile shape, persistent CTAs per SM, points per block) and writes the
+ * fastest into *out.  Runs the batch several times (the outputs are written)
+ * and synchronises the stream; call it once per kind of batch, before any
+ * capture.
+ */
+int tct_autotune_batched(const tct_map *h_maps, int32_t n_maps, const tct_params *params,
+                         void *d_ws, size_t ws_bytes, tct_stream stream, tct_tuning *out);
 
 /* ---- no-allocation variant ---------------------------------------------- */
 

@@ -121,8 +121,7 @@ __device__ void flush_tally(PointTally t, int32_t *zkeys, tct_stats *stats, bool
 // spatially sorted clouds the 32 points of a warp fall in 32 distinct cells,
 // so the match only adds work.)
 template <bool kSubtract>
-__device__ __forceinline__ int32_t cell_slot(int32_t *ctr, int cell) {
-    if (cell < 0) return -1;
+__device__ __forceinline__ int32_t cell_slot(int32_t *ctr, int64_t cell) {
     return kSubtract ? atomicSub(&ctr[cell], 1) - 1 : atomicAdd(&ctr[cell], 1);
 }
 
@@ -181,86 +180,142 @@ __global__ void k_bounds_finish(float *out6, tct_stats *stats) {
     if (t == 5 && stats) stats->z_max = key_float(k);
 }
 
-// Pass 1: histogram of points per cell plus the z bounds and tallies.
+// One point of a map: pass 1 (count) counts it in its cell and tallies the
+// bounds, pass 2 (scatter) writes its height into the cell's segment, taking
+// slots from the top down so that the counters return to zero.
+template <bool kScatter>
+__device__ __forceinline__ void visit_point(float x, float y, float z, const GridDev &g,
+                                            int64_t cell_off, int32_t *__restrict__ cnt,
+                                            const int32_t *__restrict__ start,
+                                            float *__restrict__ zs, PointTally &t) {
+    if (!finite3(x, y, z)) {
+        if (!kScatter) ++t.nonfinite;
+        return;
+    }
+    z = fold_zero(z);
+    if (!kScatter) {
+        const int32_t k = float_key(z);
+        t.zlo = min(t.zlo, k);
+        t.zhi = max(t.zhi, k);
+    }
+    const int cell = cell_of(g, x, y);
+    if (cell < 0) {
+        if (!kScatter) ++t.dropped;
+        return;
+    }
+    const int64_t gc = cell_off + cell;
+    if (!kScatter) {
+        cell_slot<false>(cnt, gc);
+    } else {
+        const int32_t slot = cell_slot<true>(cnt, gc);
+        zs[start[gc] + slot] = z;
+    }
+}
+
+// Points [p0, p1) of one map, thread `tid` of `nthreads`: groups of four
+// with vector loads where the base allows, the ragged ends one by one.
+template <bool kScatter>
+__device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int stride, bool vec,
+                                            int64_t p0, int64_t p1, int64_t tid, int64_t nthreads,
+                                            const GridDev &g, int64_t cell_off,
+                                            int32_t *__restrict__ cnt,
+                                            const int32_t *__restrict__ start,
+                                            float *__restrict__ zs, PointTally &t) {
+    int64_t q0 = 0, q1 = 0;
+    if (vec) {
+        q0 = (p0 + 3) / 4;
+        q1 = p1 / 4;
+        if (q1 < q0) q1 = q0;
+    }
+    for (int64_t q = q0 + tid; q < q1; q += nthreads) {
+        float p[4][3];
+        load4(xyz, stride, q, p);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            visit_point<kScatter>(p[u][0], p[u][1], p[u][2], g, cell_off, cnt, start, zs, t);
+    }
+    const int64_t a1 = vec ? min(4 * q0, p1) : p1;
+    for (int64_t i = p0 + tid; i < a1; i += nthreads) {
+        float p[3];
+        load1(xyz, stride, i, p);
+        visit_point<kScatter>(p[0], p[1], p[2], g, cell_off, cnt, start, zs, t);
+    }
+    if (vec) {
+        for (int64_t i = max(4 * q1, p0) + tid; i < p1; i += nthreads) {
+            float p[3];
+            load1(xyz, stride, i, p);
+            visit_point<kScatter>(p[0], p[1], p[2], g, cell_off, cnt, start, zs, t);
+        }
+    }
+}
+
+// Pass 1 of one map: histogram of points per cell, z bounds and tallies.
 __global__ void __launch_bounds__(kThreads)
 k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
         int32_t *__restrict__ cnt, int32_t *zkeys, tct_stats *stats) {
     PointTally t;
     t.init();
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t ngroups = vec ? n / 4 : 0;
-    auto visit = [&](float x, float y, float z) {
-        int cell = -1;
-        if (!finite3(x, y, z)) {
-            ++t.nonfinite;
-        } else {
-            const int32_t k = float_key(fold_zero(z));
-            t.zlo = min(t.zlo, k); t.zhi = max(t.zhi, k);
-            cell = cell_of(g, x, y);
-            if (cell < 0) ++t.dropped;
-        }
-        cell_slot<false>(cnt, cell);
-    };
-    // the loop bound is warp-uniform so that every lane joins each match
-    for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
-        const int64_t grp = base + (threadIdx.x & 31);
-        float p[4][3];
-        const bool ok = grp < ngroups;
-        if (ok) load4(xyz, stride, grp, p);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (ok) visit(p[q][0], p[q][1], p[q][2]);
-            else cell_slot<false>(cnt, -1);
-        }
-    }
-    for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
-        const int64_t i = base + (threadIdx.x & 31);
-        if (i < n) {
-            float p[3];
-            load1(xyz, stride, i, p);
-            visit(p[0], p[1], p[2]);
-        } else {
-            cell_slot<false>(cnt, -1);
-        }
-    }
+    visit_range<false>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                       (int64_t)gridDim.x * blockDim.x, g, 0, cnt, nullptr, nullptr, t);
     flush_tally(t, zkeys, stats, true);
 }
 
-// Pass 2: every finite on-grid point writes its z into its cell's segment.
-// Slots are taken from the top of the segment down, so cnt returns to zero.
+// Pass 2 of one map.
 __global__ void __launch_bounds__(kThreads)
 k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
           int32_t *__restrict__ cnt, const int32_t *__restrict__ start, float *__restrict__ zs) {
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t ngroups = vec ? n / 4 : 0;
-    auto visit = [&](float x, float y, float z) {
-        const int cell = finite3(x, y, z) ? cell_of(g, x, y) : -1;
-        const int32_t slot = cell_slot<true>(cnt, cell);
-        if (cell >= 0) zs[start[cell] + slot] = fold_zero(z);
-    };
-    for (int64_t base = tid - (threadIdx.x & 31); base < ngroups; base += nthreads) {
-        const int64_t grp = base + (threadIdx.x & 31);
-        float p[4][3];
-        const bool ok = grp < ngroups;
-        if (ok) load4(xyz, stride, grp, p);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (ok) visit(p[q][0], p[q][1], p[q][2]);
-            else cell_slot<true>(cnt, -1);
-        }
-    }
-    for (int64_t base = ngroups * 4 + tid - (threadIdx.x & 31); base < n; base += nthreads) {
-        const int64_t i = base + (threadIdx.x & 31);
-        if (i < n) {
-            float p[3];
-            load1(xyz, stride, i, p);
-            visit(p[0], p[1], p[2]);
-        } else {
-            cell_slot<true>(cnt, -1);
-        }
-    }
+    PointTally t;
+    t.init();
+    visit_range<true>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (int64_t)gridDim.x * blockDim.x, g, 0, cnt, start, zs, t);
+}
+
+// Both passes over a batch: block b serves one chunk of one map's points.
+struct PointMap {
+    const float *xyz;
+    int64_t n;
+    int32_t stride, vec;
+    GridDev g;
+    int64_t cell_off;            // first cell of the map in the concatenated arrays
+    int32_t *zkeys;
+    tct_stats *stats;
+    int32_t block_start;         // first block of the map
+};
+
+struct PointBatch {
+    int32_t n_maps;
+    int32_t chunk;               // points per block, a multiple of 4
+    PointMap maps[TCT_MAX_BATCH];
+};
+
+__device__ __forceinline__ int batch_map_of_block(const PointBatch &b) {
+    int m = 0;
+    while (m + 1 < b.n_maps && b.maps[m + 1].block_start <= (int)blockIdx.x) ++m;
+    return m;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_count_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt) {
+    const PointMap &m = b.maps[batch_map_of_block(b)];
+    const int64_t p0 = (int64_t)((int)blockIdx.x - m.block_start) * b.chunk;
+    const int64_t p1 = min(m.n, p0 + b.chunk);
+    PointTally t;
+    t.init();
+    visit_range<false>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
+                       m.cell_off, cnt, nullptr, nullptr, t);
+    flush_tally(t, m.zkeys, m.stats, true);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scatter_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt,
+                  const int32_t *__restrict__ start, float *__restrict__ zs) {
+    const PointMap &m = b.maps[batch_map_of_block(b)];
+    const int64_t p0 = (int64_t)((int)blockIdx.x - m.block_start) * b.chunk;
+    const int64_t p1 = min(m.n, p0 + b.chunk);
+    PointTally t;
+    t.init();
+    visit_range<true>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
+                      m.cell_off, cnt, start, zs, t);
 }
 
 // Exclusive scan of cnt[0, m) into start[0, m], in tiles of kScanTile.
@@ -552,6 +607,52 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     k_sort_long<<<grid_blocks(m, kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
                                                                     ws.long_count, ws.long_cells);
     count_launches(n > 0 ? 9 : 7);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int chunk,
+                                     int64_t total_cells, const Workspace &ws, cudaStream_t s) {
+    if (n_maps < 1 || n_maps > TCT_MAX_BATCH || chunk < 4 || chunk % 4) return cudaErrorInvalidValue;
+    PointBatch b;
+    b.n_maps = n_maps;
+    b.chunk = chunk;
+    int64_t blocks = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        PointMap &m = b.maps[i];
+        m.xyz = maps[i].xyz;
+        m.n = maps[i].n;
+        m.stride = maps[i].stride;
+        m.vec = (reinterpret_cast<uintptr_t>(maps[i].xyz) & 15u) == 0 ? 1 : 0;
+        m.g = grid_dev(maps[i].grid);
+        m.cell_off = maps[i].cell_off;
+        m.zkeys = maps[i].zkeys;
+        m.stats = maps[i].stats;
+        m.block_start = (int32_t)blocks;
+        blocks += (maps[i].n + chunk - 1) / chunk;
+    }
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const int64_t m = total_cells;
+    cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int32_t) * m, s);
+    if (e != cudaSuccess) return e;
+    int launches = 5;
+    if (blocks > 0) {
+        k_count_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt);
+        ++launches;
+    }
+    const int nb = (int)((m + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
+    k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
+    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
+    if (blocks > 0) {
+        k_scatter_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.zs);
+        ++launches;
+    }
+    cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
+    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        ws.start, m, ws.zs, ws.long_count, ws.long_cells);
+    k_sort_long<<<grid_blocks(m, kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                              ws.long_count, ws.long_cells);
+    count_launches(launches);
     return cudaGetLastError();
 }
 

@@ -89,17 +89,38 @@ cudaError_t launch_bounds(const float *xyz, int64_t n, int stride, float *out6,
                           tct_stats *stats, cudaStream_t s);
 cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_grid &g,
                              const Workspace &ws, tct_stats *stats, cudaStream_t s);
+// Batches: the maps' cells are concatenated (map i starts at cell_off), so one
+// scan over all of them gives every point's position in the shared zs.
+struct BatchPointsIn {
+    const float *xyz;
+    int64_t n;
+    int32_t stride;
+    tct_grid grid;
+    int64_t cell_off;
+    int32_t *zkeys;      // initialised by the caller
+    tct_stats *stats;    // zeroed by the caller
+};
+cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int chunk,
+                                     int64_t total_cells, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *ground,
                               float *ceil, cudaStream_t s);
 
 // launchers (tct_stack.cu)
+// tile: TCT_TILE_AUTO, TCT_TILE_64 or TCT_TILE_32 (build path only).
 cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
                          const int32_t *zkeys, const float *gin, const float *cin,
                          float *ground, float *ceil, float *cost, uint8_t *mask, float *aux,
-                         int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s);
+                         int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s,
+                         int tile = TCT_TILE_AUTO);
 // The incremental kernel for the build path; returns cudaErrorNotSupported
 // when no instance matches the window radii (the caller then falls back).
-cudaError_t launch_stack_inc(const StackArgs &a, cudaStream_t s);
+// tile: TCT_TILE_64 or TCT_TILE_32.
+bool inc_supported(const EvalConsts &c, int n_slices);
+cudaError_t launch_stack_inc(const StackArgs &a, int tile, cudaStream_t s);
+// One persistent launch over the tiles of n_maps maps (largest first);
+// queue must be zero when the launch starts.
+cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,
+                                 int32_t *queue, int tile, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits,
                          uint32_t flags, uint8_t *keep, tct_stats *stats, cudaStream_t s);
 

@@ -405,7 +405,7 @@ cudaError_t pick_tile(const StackArgs &a, cudaStream_t s) {
 cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
                          const int32_t *zkeys, const float *gin, const float *cin, float *ground,
                          float *ceil, float *cost, uint8_t *mask, float *aux, int32_t *upre,
-                         uint32_t *ubits, tct_stats *stats, cudaStream_t s) {
+                         uint32_t *ubits, tct_stats *stats, cudaStream_t s, int tile) {
     StackArgs a;
     a.W = g.W;
     a.H = g.H;
@@ -430,7 +430,15 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     k_stack_init<<<1, 128, 0, s>>>(upre, ubits);
     count_launches(1);
     if (lists) {
-        const cudaError_t e = launch_stack_inc(a, s);
+        if (tile == TCT_TILE_AUTO) {
+            // 64 x 64 tiles unless they leave SMs idle
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t tiles64 = (int64_t)((g.W + 63) / 64) * ((g.H + 63) / 64);
+            tile = tiles64 < sms ? TCT_TILE_32 : TCT_TILE_64;
+        }
+        const cudaError_t e = launch_stack_inc(a, tile, s);
         if (e != cudaErrorNotSupported) return e;
         return pick_tile<true, false>(a, s);
     }

@@ -26,17 +26,21 @@
 namespace tct {
 namespace {
 
-constexpr int kTW = 64, kTH = 64, kNT = 512, kNW = kNT / 32, kStrip = 8;
-static_assert(kTH == kStrip * (kNW / 2), "two 32-column halves x strips of 8 rows");
+constexpr int kStrip = 8;             // rows of a thread's inflation strip
 constexpr uint32_t kSat = 0xffffu;   // saturated 16-bit pointer offset
 
-template <int RK, int RP>
+// Tile of TW x TH cells: TW/32 column halves x TH/8 strips, one warp each.
+template <int RK, int RP, int TW, int TH>
 struct Geo {
+    static_assert(TW % 32 == 0 && TH % kStrip == 0, "tile made of 32 x 8 strips");
+    static constexpr int NHALF = TW / 32;
+    static constexpr int NW = NHALF * (TH / kStrip);
+    static constexpr int NT = 32 * NW;
     static constexpr int HE = RK + RP + 1;
-    static constexpr int EW = kTW + 2 * HE, EH = kTH + 2 * HE;    // elevation region
+    static constexpr int EW = TW + 2 * HE, EH = TH + 2 * HE;      // elevation region
     static constexpr int NE = EW * EH;
     static constexpr int GW = EW - 2, GH = EH - 2;                // gentle region
-    static constexpr int CW = kTW + 2 * RK, CH = kTH + 2 * RK;    // c^init region
+    static constexpr int CW = TW + 2 * RK, CH = TH + 2 * RK;      // c^init region
     static constexpr int EWW = (EW + 31) / 32 + 1;                // change words per row (+pad)
     static constexpr int GWW = (GW + 31) / 32 + 1;                // gentle words per row (+pad)
     static constexpr int CWW = (CW + 31) / 32 + 1;                // c^init change words (+pad)
@@ -46,6 +50,13 @@ struct Geo {
         return sizeof(float) * (2 * NE + CW * CH) + sizeof(uint32_t) * WORDS +
                ((sizeof(uint16_t) * NE + 15) / 16) * 16;
     }
+};
+
+// Shared state of the per-slice counters, kept in static shared memory.
+struct SliceCounters {
+    int32_t upre[TCT_MAX_SLICES + 1];
+    int32_t valid[TCT_MAX_SLICES + 1];
+    int32_t trav[TCT_MAX_SLICES + 1];
 };
 
 __device__ __forceinline__ float max3(float a, float b, float c) {
@@ -65,15 +76,35 @@ __device__ __forceinline__ int32_t upper_bound(const float *__restrict__ zs, int
     return s;
 }
 
-// Two CTAs per SM fit the shared memory of windows up to R_K = 8; the
-// wider ones run one CTA per SM and may use more registers.
-template <int RK, int RP>
-__global__ void __launch_bounds__(kNT, RK <= 8 ? 2 : 1)
-k_stack_inc(const __grid_constant__ StackArgs a) {
-    using G = Geo<RK, RP>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int32_t s_upre[TCT_MAX_SLICES + 1];
-    __shared__ int32_t s_valid[TCT_MAX_SLICES + 1], s_trav[TCT_MAX_SLICES + 1];
+// The per-map fields the incremental slice stack reads and writes.
+struct IncMap {
+    int32_t W, H, N;
+    float d_s, z_min;
+    int32_t zmin_from_data;
+    const int32_t *zkeys;        // ordered-int z bounds from the count pass
+    const int32_t *start;        // per-cell segments
+    const float *zs;
+    float *ground, *ceil, *cost;
+    uint8_t *mask;
+    int32_t *upre;
+    uint32_t *ubits;
+    tct_stats *stats;
+};
+
+struct IncArgs {
+    IncMap m;
+    EvalConsts c;
+};
+
+// One tile (TW x TH cells at tx0, ty0) of one map over all its slices, by
+// one CTA of Geo::NT threads.  smem is the dynamic buffer of smem_bytes();
+// the caller synchronises before the buffer is used for another tile.
+template <int RK, int RP, int TW, int TH>
+__device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c, int tx0, int ty0,
+                                           unsigned char *smem, SliceCounters &counters) {
+    using G = Geo<RK, RP, TW, TH>;
+    constexpr int kNT = G::NT, kNW = G::NW;
+    int32_t *s_upre = counters.upre, *s_valid = counters.valid, *s_trav = counters.trav;
 
     float *sEG = reinterpret_cast<float *>(smem);          // ground (state)
     float *sZC = sEG + G::NE;                                // next z = ceiling (state)
@@ -85,9 +116,7 @@ k_stack_inc(const __grid_constant__ StackArgs a) {
     uint32_t *sCIChg = sGChg + G::GH * G::GWW;
     uint16_t *sOff = reinterpret_cast<uint16_t *>(sCIChg + G::CH * G::CWW);
 
-    const EvalConsts &c = a.c;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kTH;
     const int64_t HW = (int64_t)a.W * a.H;
     const float ts2 = c.theta_s * c.theta_s;   // m^grad < theta_s  <=>  m^2 < theta_s^2
     const float inv_ts2 = c.inv_ts * c.inv_ts;
@@ -118,7 +147,7 @@ k_stack_inc(const __grid_constant__ StackArgs a) {
     }
 
     // ---- per-thread state of its strip: 8 cells in one column ----
-    const int half = warp & 1, strip = warp >> 1;
+    const int half = warp % G::NHALF, strip = warp / G::NHALF;
     const int ts = 32 * half + lane;           // tile column
     const int tr0 = kStrip * strip;            // first tile row of the strip
     const int j_out = tx0 + ts;
@@ -418,28 +447,161 @@ k_stack_inc(const __grid_constant__ StackArgs a) {
     }
 }
 
-template <int RK, int RP>
-cudaError_t run_inc(const StackArgs &a, cudaStream_t s) {
-    using G = Geo<RK, RP>;
+// Resident CTAs per SM that the tile's shared memory and 64 registers per
+// thread allow.
+template <int RK, int RP, int TW, int TH>
+struct Occupancy {
+    using G = Geo<RK, RP, TW, TH>;
+    static constexpr int by_smem = (int)(200000 / (G::smem_bytes() + 2048));
+    static constexpr int by_regs = 65536 / (64 * G::NT);
+    static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
+};
+
+template <int RK, int RP, int TW, int TH>
+__global__ void __launch_bounds__(Geo<RK, RP, TW, TH>::NT, (Occupancy<RK, RP, TW, TH>::value))
+k_stack_inc(const __grid_constant__ IncArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SliceCounters counters;
+    stack_tile<RK, RP, TW, TH>(args.m, args.c, blockIdx.x * TW, blockIdx.y * TH, smem, counters);
+}
+
+template <int RK, int RP, int TW, int TH>
+cudaError_t run_inc(const IncArgs &a, cudaStream_t s) {
+    using G = Geo<RK, RP, TW, TH>;
     const size_t smem = G::smem_bytes();
-    auto fn = k_stack_inc<RK, RP>;
+    auto fn = k_stack_inc<RK, RP, TW, TH>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH);
-    fn<<<grid, kNT, smem, s>>>(a);
+    dim3 grid((a.m.W + TW - 1) / TW, (a.m.H + TH - 1) / TH);
+    fn<<<grid, G::NT, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- batches
+//
+// One persistent launch over the tiles of many maps: each CTA takes the next
+// (map, tile) item from a queue; maps come largest first so the long tiles
+// start early.  The descriptors travel in the kernel parameters.
+
+struct BatchArgs {
+    EvalConsts c;
+    int32_t n_maps;
+    int32_t total;                       // items
+    int32_t *queue;                      // next item (zero before the launch)
+    int32_t item_start[TCT_MAX_BATCH + 1];
+    int32_t tiles_x[TCT_MAX_BATCH];
+    IncMap maps[TCT_MAX_BATCH];
+};
+
+template <int RK, int RP, int TW, int TH>
+__global__ void __launch_bounds__(Geo<RK, RP, TW, TH>::NT, (Occupancy<RK, RP, TW, TH>::value))
+k_stack_batched(const __grid_constant__ BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SliceCounters counters;
+    __shared__ int32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= b.total) break;
+        int m = 0;
+        while (m + 1 < b.n_maps && b.item_start[m + 1] <= item) ++m;
+        const int t = item - b.item_start[m];
+        const int tx = t % b.tiles_x[m], ty = t / b.tiles_x[m];
+        stack_tile<RK, RP, TW, TH>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
+        __syncthreads();
+    }
+}
+
+template <int RK, int RP, int TW, int TH>
+cudaError_t run_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
+    using G = Geo<RK, RP, TW, TH>;
+    const size_t smem = G::smem_bytes();
+    auto fn = k_stack_batched<RK, RP, TW, TH>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148, fit = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, G::NT, smem);
+    if (e != cudaSuccess) return e;
+    if (fit < 1) fit = 1;
+    int per_sm = ctas_per_sm > 0 && ctas_per_sm < fit ? ctas_per_sm : fit;
+    int grid = sms * per_sm;
+    if (grid > b.total) grid = b.total > 0 ? b.total : 1;
+    fn<<<grid, G::NT, smem, s>>>(b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+IncMap inc_map(const StackArgs &a) {
+    IncMap m;
+    m.W = a.W; m.H = a.H; m.N = a.N;
+    m.d_s = a.d_s; m.z_min = a.z_min; m.zmin_from_data = a.zmin_from_data;
+    m.zkeys = a.zkeys; m.start = a.start; m.zs = a.zs;
+    m.ground = a.ground; m.ceil = a.ceil; m.cost = a.cost; m.mask = a.mask;
+    m.upre = a.upre; m.ubits = a.ubits; m.stats = a.stats;
+    return m;
+}
+
+template <int TW, int TH>
+cudaError_t dispatch_single(const IncArgs &a, cudaStream_t s) {
+    const int RK = a.c.rk, RP = a.c.patch_radius;
+    if (RP == 2 && RK == 5) return run_inc<5, 2, TW, TH>(a, s);
+    if (RP == 2 && RK == 4) return run_inc<4, 2, TW, TH>(a, s);
+    if (RP == 2 && RK == 12) return run_inc<12, 2, TW, TH>(a, s);
+    return cudaErrorNotSupported;
+}
+
+template <int TW, int TH>
+cudaError_t dispatch_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
+    const int RK = b.c.rk, RP = b.c.patch_radius;
+    if (RP == 2 && RK == 5) return run_batched<5, 2, TW, TH>(b, ctas_per_sm, s);
+    if (RP == 2 && RK == 4) return run_batched<4, 2, TW, TH>(b, ctas_per_sm, s);
+    if (RP == 2 && RK == 12) return run_batched<12, 2, TW, TH>(b, ctas_per_sm, s);
+    return cudaErrorNotSupported;
+}
+
 }  // namespace
 
-cudaError_t launch_stack_inc(const StackArgs &a, cudaStream_t s) {
-    const int RK = a.c.rk, RP = a.c.patch_radius;
-    if (a.N > 255) return cudaErrorNotSupported;     // run starts are kept in bytes
-    if (RP == 2 && RK == 5) return run_inc<5, 2>(a, s);
-    if (RP == 2 && RK == 4) return run_inc<4, 2>(a, s);
-    if (RP == 2 && RK == 12) return run_inc<12, 2>(a, s);
-    return cudaErrorNotSupported;
+bool inc_supported(const EvalConsts &c, int n_slices) {
+    if (n_slices > 255) return false;                // run starts are kept in bytes
+    const int RK = c.rk, RP = c.patch_radius;
+    return RP == 2 && (RK == 5 || RK == 4 || RK == 12);
+}
+
+cudaError_t launch_stack_inc(const StackArgs &a, int tile, cudaStream_t s) {
+    if (!inc_supported(a.c, a.N)) return cudaErrorNotSupported;
+    IncArgs args;
+    args.m = inc_map(a);
+    args.c = a.c;
+    if (tile == TCT_TILE_32) return dispatch_single<32, 32>(args, s);
+    return dispatch_single<64, 64>(args, s);
+}
+
+cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,
+                                 int32_t *queue, int tile, int ctas_per_sm, cudaStream_t s) {
+    if (n_maps < 1 || n_maps > TCT_MAX_BATCH) return cudaErrorInvalidValue;
+    for (int i = 0; i < n_maps; ++i)
+        if (!inc_supported(c, maps[i].N)) return cudaErrorNotSupported;
+    BatchArgs b;                 // kernel parameters, copied at launch
+    b.c = c;
+    b.n_maps = n_maps;
+    b.queue = queue;
+    const int TW = tile == TCT_TILE_32 ? 32 : 64, TH = TW;
+    int total = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        b.maps[i] = inc_map(maps[i]);
+        b.item_start[i] = total;
+        b.tiles_x[i] = (maps[i].W + TW - 1) / TW;
+        total += b.tiles_x[i] * ((maps[i].H + TH - 1) / TH);
+    }
+    b.item_start[n_maps] = total;
+    b.total = total;
+    if (tile == TCT_TILE_32) return dispatch_batched<32, 32>(b, ctas_per_sm, s);
+    return dispatch_batched<64, 64>(b, ctas_per_sm, s);
 }
 
 }  // namespace tct

@@ -52,6 +52,21 @@ class TctStats(ctypes.Structure):
 
 
 STATS_BYTES = ctypes.sizeof(TctStats)
+MAX_BATCH = 64
+TILE_AUTO, TILE_64, TILE_32 = 0, 1, 2
+
+
+class TctMap(ctypes.Structure):
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("grid", TctGrid),
+                ("d_ground", ctypes.c_void_p), ("d_ceil", ctypes.c_void_p),
+                ("d_cost", ctypes.c_void_p), ("d_mask", ctypes.c_void_p),
+                ("d_keep", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
+
+
+class TctTuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("points_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 _P = ctypes.c_void_p
 _SIGNATURES = {
@@ -73,6 +88,15 @@ _SIGNATURES = {
                                                   ctypes.POINTER(TctGrid),
                                                   ctypes.POINTER(TctParams), _P, _P, _P, _P, _P,
                                                   _P, _P]),
+    "tct_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.POINTER(TctMap), ctypes.c_int32,
+                                                      ctypes.POINTER(TctParams)]),
+    "tct_build_evaluate_batched": (ctypes.c_int, [ctypes.POINTER(TctMap), ctypes.c_int32,
+                                                  ctypes.POINTER(TctParams),
+                                                  ctypes.POINTER(TctTuning), _P, ctypes.c_size_t,
+                                                  _P]),
+    "tct_autotune_batched": (ctypes.c_int, [ctypes.POINTER(TctMap), ctypes.c_int32,
+                                            ctypes.POINTER(TctParams), _P, ctypes.c_size_t, _P,
+                                            ctypes.POINTER(TctTuning)]),
     "tct_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
@@ -249,6 +273,70 @@ def tct_build_evaluate_noalloc(xyz: torch.Tensor, grid: Grid, params: dict, grou
                                              ctypes.byref(cp), _ptr(ground), _ptr(ceil),
                                              _ptr(cost), _ptr(mask), _ptr(keep), _ptr(stats),
                                              _stream()))
+
+
+@dataclass
+class MapBuffers:
+    """One map of a batch: its points and its own output tensors (device)."""
+    xyz: torch.Tensor
+    grid: Grid
+    ground: torch.Tensor
+    ceil: torch.Tensor
+    cost: torch.Tensor
+    mask: torch.Tensor
+    keep: torch.Tensor
+    stats: torch.Tensor | None = None
+
+    @staticmethod
+    def allocate(xyz: torch.Tensor, grid: Grid) -> "MapBuffers":
+        dev = xyz.device
+        return MapBuffers(xyz, grid,
+                          torch.empty(grid.shape, dtype=torch.float32, device=dev),
+                          torch.empty(grid.shape, dtype=torch.float32, device=dev),
+                          torch.empty(grid.shape, dtype=torch.float32, device=dev),
+                          torch.empty(grid.shape, dtype=torch.uint8, device=dev),
+                          torch.empty(grid.n_slices, dtype=torch.uint8, device=dev),
+                          torch.zeros(STATS_BYTES, dtype=torch.uint8, device=dev))
+
+
+def _maps_c(maps: list[MapBuffers]):
+    arr = (TctMap * len(maps))()
+    for i, m in enumerate(maps):
+        n, stride = _points(m.xyz)
+        arr[i] = TctMap(m.xyz.data_ptr(), n, stride, 0, m.grid.c(), m.ground.data_ptr(),
+                        m.ceil.data_ptr(), m.cost.data_ptr(), m.mask.data_ptr(),
+                        m.keep.data_ptr(), m.stats.data_ptr() if m.stats is not None else None)
+    return arr
+
+
+def tct_workspace_bytes_batched(maps: list[MapBuffers], params: dict) -> int:
+    arr = _maps_c(maps)
+    cp = _params_c(params)
+    n = load().tct_workspace_bytes_batched(arr, len(maps), ctypes.byref(cp))
+    if n == 0:
+        raise TctError("tct_workspace_bytes_batched", -1)
+    return n
+
+
+def tct_build_evaluate_batched(maps: list[MapBuffers], params: dict, ws: torch.Tensor,
+                               tuning: TctTuning | None = None):
+    arr = _maps_c(maps)
+    cp = _params_c(params)
+    _check("tct_build_evaluate_batched",
+           load().tct_build_evaluate_batched(arr, len(maps), ctypes.byref(cp),
+                                             ctypes.byref(tuning) if tuning is not None else None,
+                                             _ptr(ws), ws.numel() * ws.element_size(), _stream()))
+
+
+def tct_autotune_batched(maps: list[MapBuffers], params: dict, ws: torch.Tensor) -> TctTuning:
+    arr = _maps_c(maps)
+    cp = _params_c(params)
+    out = TctTuning()
+    _check("tct_autotune_batched",
+           load().tct_autotune_batched(arr, len(maps), ctypes.byref(cp), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream(),
+                                       ctypes.byref(out)))
+    return out
 
 
 # --------------------------------------------------------------- helpers
