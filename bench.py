@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--workload", choices=["parking", "parking-small", "building"],
                     default="parking")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-map batched-versus-plain measurement")
     return ap.parse_args()
 
 
@@ -181,6 +183,71 @@ def cpu_baseline(sc, params):
     return {"value": len(sc.points) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": round(dt, 3),
             "sample": "the full workload once (build, evaluate with fragility bounds, chain)"}
+
+
+def batched_vs_plain(dev, params, steps):
+    """64 maps of uneven size (points log-uniform 50k-4M, sides 128-1024 cells,
+    4-48 slices): sequential single-map calls against one batched call (tuned by
+    the library's autotuner) and against a CUDA-graph replay of that call."""
+    import torch
+    from paper_2403_07631_gb300 import scenes, tct
+    scs = scenes.batched_maps()
+    maps = []
+    for sc in scs:
+        g = tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, sc.n_slices, 0.0, True)
+        maps.append(tct.MapBuffers.allocate(torch.from_numpy(sc.points).to(dev), g))
+    P = sum(len(sc.points) for sc in scs)
+    SC = sum(sc.W * sc.H * sc.n_slices for sc in scs)
+    ws_plain = torch.empty(max(tct.tct_workspace_bytes(m.grid, m.xyz.shape[0], params) for m in maps),
+                           dtype=torch.uint8, device=dev)
+    ws = torch.empty(tct.tct_workspace_bytes_batched(maps, params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for m in maps:
+            tct.tct_build_evaluate(m.xyz, m.grid, params, ws_plain, m.ground, m.ceil, m.cost,
+                                   m.mask, m.keep, m.stats)
+
+    tuning = tct.tct_autotune_batched(maps, params, ws)
+
+    def batched():
+        tct.tct_build_evaluate_batched(maps, params, ws, tuning)
+
+    def timed(fn, n):
+        out = []
+        for i in range(n + 2):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if i >= 2:
+                out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    t_plain = timed(plain, steps)
+    t_batch = timed(batched, steps)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batched()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        batched()
+    t_graph = timed(graph.replay, steps)
+    return {"workload": "64 buildings, seeds 3000-3063, %.1fM points, %.0fM slice-cells" % (P / 1e6, SC / 1e6),
+            "plain_ms": t_plain, "batched_ms": t_batch, "graph_replay_ms": t_graph,
+            "batched_speedup": t_plain / t_batch, "graph_speedup": t_plain / t_graph,
+            "batched_mpoints_per_s": P / (t_graph * 1e-3) / 1e6,
+            "batched_slice_cells_per_s": SC / (t_graph * 1e-3),
+            "path_roofline_frac": (12 * P + 13 * SC) / (t_graph * 1e-3) / 1e9 / measured_peak_gbs()[0],
+            "tuning": {"tile": {1: "64x64", 2: "32x32"}.get(tuning.tile, "auto"),
+                       "ctas_per_sm": tuning.ctas_per_sm,
+                       "points_per_block": tuning.points_per_block}}
 
 
 def run_reference(args):
@@ -331,6 +398,10 @@ def main():
         "clocks": clocks,
         "kept_slices": int(st.n_kept),
     }
+    if not args.no_batched:
+        del ws, ground, ceil, cost, mask, keep
+        torch.cuda.empty_cache()
+        out["batched_vs_plain"] = batched_vs_plain(dev, params, min(args.steps, 5))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, params)
     if world > 1:

@@ -16,6 +16,9 @@ out.  Every function cites the passage of the paper it restates:
 - ``evaluate``         Sec. III-B, Eq. 1-6 (interval, gradient, terrain and
                        initial costs, inflation, traversable mask)
 - ``simplify``         Sec. III-C, Eq. 7-9 (sequential slice-removal chain)
+- ``sample``           the cost / elevation queries C(q), e^G(q) of Eq. 10 (bilinear,
+                       with the gradient of the interpolant)
+- ``refine``           descent on path waypoints with those queries (an objective of ours)
 """
 from __future__ import annotations
 
@@ -81,8 +84,12 @@ def _load():
         lib.oracle_evaluate.argtypes = [ctypes.POINTER(OracleGrid), ctypes.POINTER(OracleParams),
                                         P, P, P, P, P, P]
         lib.oracle_simplify.argtypes = [i32, i32, i32, P, P, P, ctypes.c_double, i32, P, P, P]
+        lib.oracle_sample.argtypes = [ctypes.POINTER(OracleGrid), P, i32, P, P, i64, P, P]
+        lib.oracle_refine.argtypes = [ctypes.POINTER(OracleGrid), P, P, i32, i32, i32,
+                                      ctypes.c_double, ctypes.c_double, P]
         for f in ("oracle_plane_heights", "oracle_bounds", "oracle_derive_grid", "oracle_build",
-                  "oracle_kernel", "oracle_evaluate", "oracle_simplify"):
+                  "oracle_kernel", "oracle_evaluate", "oracle_simplify", "oracle_sample",
+                  "oracle_refine"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -225,3 +232,30 @@ def simplify(eG: np.ndarray, cT: np.ndarray, c_b: float, fragile: np.ndarray | N
                                  _ptr(counts))
     _check(rc, "simplify")
     return (keep, bool(robust[0]), counts) if want_counts else (keep, bool(robust[0]))
+
+
+def sample(g: Grid, layer: np.ndarray, xy: np.ndarray, slice_idx: np.ndarray,
+           is_ground: bool = False):
+    """Bilinear query of slice `slice_idx[t]` of `layer` ([N,H,W] float32) at xy[t];
+    returns (values float64 [Q], gradient float64 [Q,2])."""
+    layer = np.ascontiguousarray(layer, np.float32)
+    xy = np.ascontiguousarray(xy, np.float32).reshape(-1, 2)
+    sl = np.ascontiguousarray(slice_idx, np.int32).reshape(-1)
+    q = len(xy)
+    out = np.empty(q, np.float64)
+    grad = np.empty((q, 2), np.float64)
+    _check(_load().oracle_sample(ctypes.byref(g.c()), _ptr(layer), int(is_ground), _ptr(xy),
+                                 _ptr(sl), q, _ptr(out), _ptr(grad)), "sample")
+    return out, grad
+
+
+def refine(g: Grid, cost: np.ndarray, slice_idx: np.ndarray, xy: np.ndarray, steps: int,
+           eta: float, lam: float) -> np.ndarray:
+    """`steps` descent steps on every path of xy [paths, len, 2]; returns the new xy (float64)."""
+    cost = np.ascontiguousarray(cost, np.float32)
+    X = np.array(xy, dtype=np.float64, order="C")
+    paths, length = X.shape[0], X.shape[1]
+    sl = np.ascontiguousarray(slice_idx, np.int32).reshape(paths, length)
+    _check(_load().oracle_refine(ctypes.byref(g.c()), _ptr(cost), _ptr(sl), paths, length, steps,
+                                 float(eta), float(lam), _ptr(X)), "refine")
+    return X

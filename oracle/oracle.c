@@ -521,3 +521,105 @@ int oracle_simplify(int32_t N, int32_t H, int32_t W, const float *eG, const doub
     if (robust) robust[0] = (uint8_t)ok;
     return ORACLE_OK;
 }
+
+/*
+ * Cost and elevation queries of the trajectory program (Sec. III-E, Eq. 10
+ * uses C(q) and e^G(q)): bilinear interpolation of slice k on the lattice of
+ * cell centres.  u = (x - x0)/r_g - 1/2, v = (y - y0)/r_g - 1/2, clamped to
+ * [0, W-1] x [0, H-1]; the 2x2 stencil starts at (min(floor(v), H-2),
+ * min(floor(u), W-2)).  Invalid ground (-inf) reads as h_k - d_s.  The
+ * gradient is that of the interpolant; along an axis where the query was
+ * clamped it is zero.  out: value [q]; grad: [q][2] (d/dx, d/dy), may be NULL.
+ * Slices outside [0, N) and non-finite queries give NaN.
+ */
+static double oracle_layer_at(const float *L, int W, int i, int j, double fill)
+{
+    const double v = (double)L[(int64_t)i * W + j];
+    return v > -INFINITY ? v : fill;
+}
+
+int oracle_sample(const oracle_grid *g, const float *layer, int32_t is_ground, const float *xy,
+                  const int32_t *slice, int64_t q, double *out, double *grad)
+{
+    if (!g || !layer || !xy || !slice || !out || q < 0) return ORACLE_EINVAL;
+    const int W = g->W, H = g->H;
+    const int64_t HW = (int64_t)W * H;
+    const double r = (double)g->res;
+    for (int64_t t = 0; t < q; ++t) {
+        const double x = xy[2 * t], y = xy[2 * t + 1];
+        const int k = slice[t];
+        if (k < 0 || k >= g->N || !isfinite(x) || !isfinite(y)) {
+            out[t] = NAN;
+            if (grad) grad[2 * t] = grad[2 * t + 1] = NAN;
+            continue;
+        }
+        const double fill = is_ground ? (double)plane_height(g, k) - (double)g->d_s : 0.0;
+        const float *L = layer + (int64_t)k * HW;
+        double u = (x - (double)g->x0) / r - 0.5, v = (y - (double)g->y0) / r - 0.5;
+        int cu = 0, cv = 0;                     /* clamped along x / y */
+        if (u < 0.0) { u = 0.0; cu = 1; }
+        if (u > W - 1) { u = W - 1; cu = 1; }
+        if (v < 0.0) { v = 0.0; cv = 1; }
+        if (v > H - 1) { v = H - 1; cv = 1; }
+        int j0 = (int)floor(u), i0 = (int)floor(v);
+        if (j0 > W - 2) j0 = W - 2;
+        if (i0 > H - 2) i0 = H - 2;
+        if (j0 < 0) j0 = 0;
+        if (i0 < 0) i0 = 0;
+        const int j1 = W > 1 ? j0 + 1 : j0, i1 = H > 1 ? i0 + 1 : i0;
+        const double fu = W > 1 ? u - j0 : 0.0, fv = H > 1 ? v - i0 : 0.0;
+        const double c00 = oracle_layer_at(L, W, i0, j0, fill), c01 = oracle_layer_at(L, W, i0, j1, fill);
+        const double c10 = oracle_layer_at(L, W, i1, j0, fill), c11 = oracle_layer_at(L, W, i1, j1, fill);
+        out[t] = (1 - fu) * (1 - fv) * c00 + fu * (1 - fv) * c01 + (1 - fu) * fv * c10 + fu * fv * c11;
+        if (grad) {
+            grad[2 * t] = (cu || W < 2) ? 0.0 : ((1 - fv) * (c01 - c00) + fv * (c11 - c10)) / r;
+            grad[2 * t + 1] = (cv || H < 2) ? 0.0 : ((1 - fu) * (c10 - c00) + fu * (c11 - c01)) / r;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/*
+ * Gradient-based refinement of waypoint paths on one tomogram (an objective
+ * of ours that uses the cost query C(q) of Eq. 10): for each path of `len`
+ * waypoints (fixed end points), `steps` descent steps of size eta on
+ *   J = sum_w c^T(x_w) + lambda sum_{w=1}^{len-2} |x_{w+1} - 2 x_w + x_{w-1}|^2,
+ * every waypoint keeping the slice it starts on.  xy: [paths][len][2], updated
+ * in place (double).
+ */
+int oracle_refine(const oracle_grid *g, const float *cost, const int32_t *slice, int32_t paths,
+                  int32_t len, int32_t steps, double eta, double lambda, double *xy)
+{
+    if (!g || !cost || !slice || !xy || paths < 0 || len < 2 || steps < 0) return ORACLE_EINVAL;
+    double *gr = (double *)malloc(sizeof(double) * 2 * len);
+    double *d2 = (double *)malloc(sizeof(double) * 2 * len);
+    float *pf = (float *)malloc(sizeof(float) * 2 * len);
+    double *val = (double *)malloc(sizeof(double) * len);
+    if (!gr || !d2 || !pf || !val) { free(gr); free(d2); free(pf); free(val); return ORACLE_ENOMEM; }
+    for (int32_t p = 0; p < paths; ++p) {
+        double *X = xy + (int64_t)p * len * 2;
+        const int32_t *S = slice + (int64_t)p * len;
+        for (int32_t s = 0; s < steps; ++s) {
+            /* the sampler reads float coordinates, as the GPU does */
+            for (int32_t w = 0; w < 2 * len; ++w) pf[w] = (float)X[w];
+            int64_t nq = len;
+            oracle_sample(g, cost, 0, pf, S, nq, val, gr);
+            for (int32_t w = 0; w < 2 * len; ++w) d2[w] = 0.0;
+            for (int32_t w = 1; w < len - 1; ++w)
+                for (int a = 0; a < 2; ++a)
+                    d2[2 * w + a] = X[2 * (w + 1) + a] - 2 * X[2 * w + a] + X[2 * (w - 1) + a];
+            for (int32_t w = 1; w < len - 1; ++w) {
+                for (int a = 0; a < 2; ++a) {
+                    double sm = -2.0 * d2[2 * w + a];
+                    if (w - 1 >= 1) sm += d2[2 * (w - 1) + a];
+                    if (w + 1 <= len - 2) sm += d2[2 * (w + 1) + a];
+                    gr[2 * w + a] += 2.0 * lambda * sm;
+                }
+            }
+            for (int32_t w = 1; w < len - 1; ++w)
+                for (int a = 0; a < 2; ++a) X[2 * w + a] -= eta * gr[2 * w + a];
+        }
+    }
+    free(gr); free(d2); free(pf); free(val);
+    return ORACLE_OK;
+}
