@@ -45,12 +45,14 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 
 /* device-side status bits (tct_stats.status) */
 #define TCT_DEV_NONFINITE 1            /* some points were NaN/inf: skipped  */
+#define TCT_DEV_BAD_QUERY 2            /* a query had a bad slice or was NaN */
 
 /* ---- limits -------------------------------------------------------------- */
 #define TCT_MAX_SLICES 127             /* N; keeps the uniqueness matrix at 128 bits per slice */
 #define TCT_MAX_KERNEL_RADIUS 15       /* inflation window radius in cells   */
 #define TCT_MAX_PATCH_RADIUS 4         /* p_s patch radius in cells          */
-#define TCT_MAX_POINTS 2000000000LL    /* points per call                    */
+#define TCT_MAX_POINTS 2000000000LL    /* points (or queries) per call       */
+#define TCT_MAX_PATH_LEN 2048          /* waypoints per path of tct_refine_paths */
 
 #define TCT_MAX_BATCH 64               /* maps per batched call              */
 
@@ -176,6 +178,47 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
                        const tct_params *params, void *d_ws, size_t ws_bytes,
                        float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
                        uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
+
+/* ---- queries (Sec. III-E, Eq. 10: C(q), e^G(q)) ------------------------- */
+
+/*
+ * Cost and ground elevation at q query points: query t reads slice
+ * d_slice[t] (an original slice index) at d_xy[2t], d_xy[2t+1] (world x, y),
+ * interpolating bilinearly between cell centres (u = (x-x0)/res - 1/2,
+ * v = (y-y0)/res - 1/2, clamped to the grid).  Invalid ground reads as
+ * h_k - d_s, so grid->z_min must be the z_min the layers were built with
+ * (tct_stats.z_min when TCT_GRID_ZMIN_FROM_DATA).  d_cost / d_ground are the
+ * [N][H][W] layers; either output may be NULL.  A query with a slice outside
+ * [0, N) or a non-finite coordinate gives NaN and sets TCT_DEV_BAD_QUERY in
+ * d_stats (may be NULL).
+ */
+int tct_sample_cost(const tct_grid *grid, const float *d_cost, const float *d_ground,
+                    const float *d_xy, const int32_t *d_slice, int64_t q, float *d_cost_out,
+                    float *d_elev_out, tct_stats *d_stats, tct_stream stream);
+
+/*
+ * Adjoint of tct_sample_cost: d_gxy[t] = d_gcost[t] * grad C(q_t) +
+ * d_gelev[t] * grad e^G(q_t), the gradient of the bilinear interpolant (zero
+ * along an axis where the query was clamped).  Either of d_gcost / d_gelev
+ * may be NULL (treated as zero).  d_gxy: [q][2].
+ */
+int tct_sample_cost_backward(const tct_grid *grid, const float *d_cost, const float *d_ground,
+                             const float *d_xy, const int32_t *d_slice, int64_t q,
+                             const float *d_gcost, const float *d_gelev, float *d_gxy,
+                             tct_stream stream);
+
+/*
+ * Gradient refinement of waypoint paths on an evaluated tomogram (an
+ * objective of this library that uses the queries above): for each of
+ * `paths` paths of `len` waypoints (d_xy [paths][len][2], updated in place;
+ * d_slice [paths][len]), `steps` descent steps of size eta on
+ *   J = sum_w C(x_w) + lambda sum_{w=1}^{len-2} |x_{w+1} - 2 x_w + x_{w-1}|^2
+ * with both end points fixed.  One launch for all steps.  len <=
+ * TCT_MAX_PATH_LEN.
+ */
+int tct_refine_paths(const tct_grid *grid, const float *d_cost, const int32_t *d_slice,
+                     int32_t paths, int32_t len, int32_t steps, float eta, float lambda,
+                     float *d_xy, tct_stream stream);
 
 /* ---- batches of maps ---------------------------------------------------- */
 

@@ -23,6 +23,8 @@ GRID_ZMIN_FROM_DATA = 1
 KEEP_ENDS = 1
 ALLOW_COARSE = 2
 DEV_NONFINITE = 1
+DEV_BAD_QUERY = 2
+MAX_PATH_LEN = 2048
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -88,6 +90,13 @@ _SIGNATURES = {
                                                   ctypes.POINTER(TctGrid),
                                                   ctypes.POINTER(TctParams), _P, _P, _P, _P, _P,
                                                   _P, _P]),
+    "tct_sample_cost": (ctypes.c_int, [ctypes.POINTER(TctGrid), _P, _P, _P, _P, ctypes.c_int64,
+                                       _P, _P, _P, _P]),
+    "tct_sample_cost_backward": (ctypes.c_int, [ctypes.POINTER(TctGrid), _P, _P, _P, _P,
+                                                ctypes.c_int64, _P, _P, _P, _P]),
+    "tct_refine_paths": (ctypes.c_int, [ctypes.POINTER(TctGrid), _P, _P, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                        ctypes.c_float, _P, _P]),
     "tct_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.POINTER(TctMap), ctypes.c_int32,
                                                       ctypes.POINTER(TctParams)]),
     "tct_build_evaluate_batched": (ctypes.c_int, [ctypes.POINTER(TctMap), ctypes.c_int32,
@@ -273,6 +282,81 @@ def tct_build_evaluate_noalloc(xyz: torch.Tensor, grid: Grid, params: dict, grou
                                              ctypes.byref(cp), _ptr(ground), _ptr(ceil),
                                              _ptr(cost), _ptr(mask), _ptr(keep), _ptr(stats),
                                              _stream()))
+
+
+def _queries(xy: torch.Tensor, slice_idx: torch.Tensor):
+    if xy.dtype != torch.float32 or xy.shape[-1] != 2 or not xy.is_contiguous():
+        raise ValueError("query points must be a contiguous [..., 2] float32 tensor")
+    if slice_idx.dtype != torch.int32 or not slice_idx.is_contiguous():
+        raise ValueError("slice indices must be a contiguous int32 tensor")
+    q = xy.numel() // 2
+    if slice_idx.numel() != q:
+        raise ValueError("one slice index per query point")
+    return q
+
+
+def tct_sample_cost(grid: Grid, cost: torch.Tensor | None, ground: torch.Tensor | None,
+                    xy: torch.Tensor, slice_idx: torch.Tensor, cost_out: torch.Tensor | None,
+                    elev_out: torch.Tensor | None, stats: torch.Tensor | None = None):
+    q = _queries(xy, slice_idx)
+    _check("tct_sample_cost",
+           load().tct_sample_cost(ctypes.byref(grid.c()), _ptr(cost), _ptr(ground), _ptr(xy),
+                                  _ptr(slice_idx), q, _ptr(cost_out), _ptr(elev_out), _ptr(stats),
+                                  _stream()))
+
+
+def tct_sample_cost_backward(grid: Grid, cost: torch.Tensor | None, ground: torch.Tensor | None,
+                             xy: torch.Tensor, slice_idx: torch.Tensor,
+                             gcost: torch.Tensor | None, gelev: torch.Tensor | None,
+                             gxy: torch.Tensor):
+    q = _queries(xy, slice_idx)
+    _check("tct_sample_cost_backward",
+           load().tct_sample_cost_backward(ctypes.byref(grid.c()), _ptr(cost), _ptr(ground),
+                                           _ptr(xy), _ptr(slice_idx), q, _ptr(gcost),
+                                           _ptr(gelev), _ptr(gxy), _stream()))
+
+
+def tct_refine_paths(grid: Grid, cost: torch.Tensor, slice_idx: torch.Tensor, xy: torch.Tensor,
+                     steps: int, eta: float, lam: float):
+    """In place: `steps` descent steps on every path of xy [paths, len, 2]."""
+    if xy.dim() != 3:
+        raise ValueError("paths must be [paths, len, 2]")
+    _queries(xy, slice_idx)
+    _check("tct_refine_paths",
+           load().tct_refine_paths(ctypes.byref(grid.c()), _ptr(cost), _ptr(slice_idx),
+                                   xy.shape[0], xy.shape[1], steps, eta, lam, _ptr(xy),
+                                   _stream()))
+
+
+class SampleCost(torch.autograd.Function):
+    """Differentiable C(q), e^G(q): forward and backward are the library's
+    tct_sample_cost and tct_sample_cost_backward kernels.  Only the query
+    coordinates receive a gradient."""
+
+    @staticmethod
+    def forward(ctx, xy, slice_idx, cost, ground, grid):
+        xy = xy.contiguous()
+        c = torch.empty(xy.shape[:-1], dtype=torch.float32, device=xy.device)
+        e = torch.empty(xy.shape[:-1], dtype=torch.float32, device=xy.device)
+        tct_sample_cost(grid, cost, ground, xy, slice_idx, c, e)
+        ctx.save_for_backward(xy, slice_idx, cost, ground)
+        ctx.grid = grid
+        return c, e
+
+    @staticmethod
+    def backward(ctx, gc, ge):
+        xy, slice_idx, cost, ground = ctx.saved_tensors
+        gxy = torch.empty_like(xy)
+        tct_sample_cost_backward(ctx.grid, cost, ground, xy, slice_idx,
+                                 None if gc is None else gc.contiguous(),
+                                 None if ge is None else ge.contiguous(), gxy)
+        return gxy, None, None, None, None
+
+
+def sample_cost(xy: torch.Tensor, slice_idx: torch.Tensor, cost: torch.Tensor,
+                ground: torch.Tensor, grid: Grid):
+    """(cost, elevation) at the queries, differentiable with respect to xy."""
+    return SampleCost.apply(xy, slice_idx, cost, ground, grid)
 
 
 @dataclass
