@@ -14,7 +14,7 @@ namespace {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cnt, start, partial, zs, scratch, long_count, long_cells, zkeys, upre, ubits, stats, total;
+    size_t cnt, start, partial, zs, scratch, long_count, long_cells, zkeys, upre, ubits, stats, queue, total;
 };
 
 Layout layout(const tct_grid &g, int64_t n_points) {
@@ -33,6 +33,7 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     L.upre = o; o = align_up(o + 4 * (TCT_MAX_SLICES + 1));
     L.ubits = o; o = align_up(o + 16 * (TCT_MAX_SLICES + 1));
     L.stats = o; o = align_up(o + sizeof(tct_stats));
+    L.queue = o; o = align_up(o + 4);
     L.total = o;
     return L;
 }
@@ -92,6 +93,7 @@ Workspace carve(void *base, const tct_grid &g, int64_t n_points) {
     w.upre = reinterpret_cast<int32_t *>(b + L.upre);
     w.ubits = reinterpret_cast<uint32_t *>(b + L.ubits);
     w.stats = reinterpret_cast<tct_stats *>(b + L.stats);
+    w.queue = reinterpret_cast<int32_t *>(b + L.queue);
     w.bytes = L.total;
     return w;
 }

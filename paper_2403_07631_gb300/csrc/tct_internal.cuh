@@ -42,6 +42,7 @@ struct Workspace {
     int32_t *upre;      // [128]  per slice: bits [0, upre) of the uniqueness row set
     uint32_t *ubits;    // [128][4] per slice: further uniqueness bits
     tct_stats *stats;   // fallback stats block when the caller passes none
+    int32_t *queue;     // [1]    tile queue of the persistent slice-stack kernel
     size_t bytes;
 };
 
@@ -116,7 +117,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
 // when no instance matches the window radii (the caller then falls back).
 // tile: TCT_TILE_64 or TCT_TILE_32.
 bool inc_supported(const EvalConsts &c, int n_slices);
-cudaError_t launch_stack_inc(const StackArgs &a, int tile, cudaStream_t s);
+cudaError_t launch_stack_inc(const StackArgs &a, int32_t *queue, int tile, cudaStream_t s);
 // One persistent launch over the tiles of n_maps maps (largest first);
 // queue must be zero when the launch starts.
 cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,

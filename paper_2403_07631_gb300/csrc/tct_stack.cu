@@ -349,8 +349,9 @@ __global__ void k_chain(int n_slices, const int32_t *upre, const uint32_t *ubits
     stats->n_kept = kept;
 }
 
-__global__ void k_stack_init(int32_t *upre, uint32_t *ubits) {
+__global__ void k_stack_init(int32_t *upre, uint32_t *ubits, int32_t *queue) {
     const int i = threadIdx.x;
+    if (i == 0 && queue) *queue = 0;
     if (i <= TCT_MAX_SLICES) {
         upre[i] = 0;
         ubits[4 * i] = ubits[4 * i + 1] = ubits[4 * i + 2] = ubits[4 * i + 3] = 0;
@@ -427,7 +428,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.ubits = ubits;
     a.stats = stats;
     a.c = c;
-    k_stack_init<<<1, 128, 0, s>>>(upre, ubits);
+    k_stack_init<<<1, 128, 0, s>>>(upre, ubits, lists ? lists->queue : nullptr);
     count_launches(1);
     if (lists) {
         if (tile == TCT_TILE_AUTO) {
@@ -438,7 +439,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
             const int64_t tiles64 = (int64_t)((g.W + 63) / 64) * ((g.H + 63) / 64);
             tile = tiles64 < sms ? TCT_TILE_32 : TCT_TILE_64;
         }
-        const cudaError_t e = launch_stack_inc(a, tile, s);
+        const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
         if (e != cudaErrorNotSupported) return e;
         return pick_tile<true, false>(a, s);
     }

@@ -1,540 +1,12 @@
-// tct_stack_inc.cu -- the build-path slice stack, incremental over slices.
-//
-// Same computation as k_stack in tct_stack.cu (Sec. III-B Eq. 1-6 per slice,
-// the uniqueness bits of Sec. III-C), specialised for compile-time window
-// radii and organised around one observation: consecutive tomogram slices
-// differ only where the plane passed a point (the redundancy Sec. III-C
-// removes afterwards).  The CTA keeps, in shared memory, the state of every
-// stage for its 64 x 64 tile and the halo and, slice after slice,
-//   1. advances each cell's pointer into its sorted z segment and marks, in
-//      per-row bit words, the cells whose ground or ceiling changed;
-//   2. recomputes the gentle flags (Eq. 2) only in 32-column row blocks whose
-//      ground stencil changed;
-//   3. recomputes c^init (Eq. 1, 3-5) only where one of its inputs changed,
-//      marking the cells whose value changed;
-//   4. re-inflates (Eq. 6) a warp's 32 x 8 strip only when a c^init in its
-//      window changed, otherwise keeps the previous c^T (bit-identical
-//      inputs give bit-identical results),
-// and writes all four layers of every slice.  Work follows the changes,
-// while the writes of every slice's layers (the algorithmic bytes) are
-// always done.
-#include <cuda_runtime.h>
-#include <math.h>
-
-#include "tct_internal.cuh"
+// tct_stack_inc.cu -- dispatch of the incremental slice stack (tct_stack_inc.cuh)
+// to its compiled window radii; one map is a batch of one.
+#include "tct_stack_inc.cuh"
 
 namespace tct {
 namespace {
 
-constexpr int kStrip = 8;             // rows of a thread's inflation strip
-constexpr uint32_t kSat = 0xffffu;   // saturated 16-bit pointer offset
-
-// Tile of TW x TH cells: TW/32 column halves x TH/8 strips, one warp each.
-template <int RK, int RP, int TW, int TH>
-struct Geo {
-    static_assert(TW % 32 == 0 && TH % kStrip == 0, "tile made of 32 x 8 strips");
-    static constexpr int NHALF = TW / 32;
-    static constexpr int NW = NHALF * (TH / kStrip);
-    static constexpr int NT = 32 * NW;
-    static constexpr int HE = RK + RP + 1;
-    static constexpr int EW = TW + 2 * HE, EH = TH + 2 * HE;      // elevation region
-    static constexpr int NE = EW * EH;
-    static constexpr int GW = EW - 2, GH = EH - 2;                // gentle region
-    static constexpr int CW = TW + 2 * RK, CH = TH + 2 * RK;      // c^init region
-    static constexpr int EWW = (EW + 31) / 32 + 1;                // change words per row (+pad)
-    static constexpr int GWW = (GW + 31) / 32 + 1;                // gentle words per row (+pad)
-    static constexpr int CWW = (CW + 31) / 32 + 1;                // c^init change words (+pad)
-    static constexpr int GPASS = (GW + 31) / 32, CPASS = (CW + 31) / 32;
-    static constexpr int WORDS = 4 * EH * EWW + 2 * GH * GWW + CH * CWW;
-    static constexpr size_t smem_bytes() {
-        return sizeof(float) * (2 * NE + CW * CH) + sizeof(uint32_t) * WORDS +
-               ((sizeof(uint16_t) * NE + 15) / 16) * 16;
-    }
-};
-
-// Shared state of the per-slice counters, kept in static shared memory.
-struct SliceCounters {
-    int32_t upre[TCT_MAX_SLICES + 1];
-    int32_t valid[TCT_MAX_SLICES + 1];
-    int32_t trav[TCT_MAX_SLICES + 1];
-};
-
-__device__ __forceinline__ float max3(float a, float b, float c) {
-    float d;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-
-// Index of the first height greater than z in the sorted segment [s, e).
-__device__ __forceinline__ int32_t upper_bound(const float *__restrict__ zs, int32_t s, int32_t e,
-                                               float z) {
-    while (s < e) {
-        const int32_t m = s + ((e - s) >> 1);
-        if (zs[m] <= z) s = m + 1;
-        else e = m;
-    }
-    return s;
-}
-
-// The per-map fields the incremental slice stack reads and writes.
-struct IncMap {
-    int32_t W, H, N;
-    float d_s, z_min;
-    int32_t zmin_from_data;
-    const int32_t *zkeys;        // ordered-int z bounds from the count pass
-    const int32_t *start;        // per-cell segments
-    const float *zs;
-    float *ground, *ceil, *cost;
-    uint8_t *mask;
-    int32_t *upre;
-    uint32_t *ubits;
-    tct_stats *stats;
-};
-
-struct IncArgs {
-    IncMap m;
-    EvalConsts c;
-};
-
-// One tile (TW x TH cells at tx0, ty0) of one map over all its slices, by
-// one CTA of Geo::NT threads.  smem is the dynamic buffer of smem_bytes();
-// the caller synchronises before the buffer is used for another tile.
-template <int RK, int RP, int TW, int TH>
-__device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c, int tx0, int ty0,
-                                           unsigned char *smem, SliceCounters &counters) {
-    using G = Geo<RK, RP, TW, TH>;
-    constexpr int kNT = G::NT, kNW = G::NW;
-    int32_t *s_upre = counters.upre, *s_valid = counters.valid, *s_trav = counters.trav;
-
-    float *sEG = reinterpret_cast<float *>(smem);          // ground (state)
-    float *sZC = sEG + G::NE;                                // next z = ceiling (state)
-    float *sCI = sZC + G::NE;                                // c^init (state)
-    uint32_t *sChgG0 = reinterpret_cast<uint32_t *>(sCI + G::CW * G::CH);   // ground changed, 2 buffers
-    uint32_t *sChgC0 = sChgG0 + 2 * G::EH * G::EWW;          // ceiling changed, 2 buffers
-    uint32_t *sGB = sChgC0 + 2 * G::EH * G::EWW;             // gentle bits (state)
-    uint32_t *sGChg = sGB + G::GH * G::GWW;
-    uint32_t *sCIChg = sGChg + G::GH * G::GWW;
-    uint16_t *sOff = reinterpret_cast<uint16_t *>(sCIChg + G::CH * G::CWW);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t HW = (int64_t)a.W * a.H;
-    const float ts2 = c.theta_s * c.theta_s;   // m^grad < theta_s  <=>  m^2 < theta_s^2
-    const float inv_ts2 = c.inv_ts * c.inv_ts;
-
-    for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
-        s_upre[i] = 0;
-        s_valid[i] = 0;
-        s_trav[i] = 0;
-    }
-    for (int i = tid; i < G::WORDS; i += kNT) sChgG0[i] = 0;
-    for (int e = tid; e < G::NE; e += kNT) {
-        const int r = e / G::EW, s = e - r * G::EW;
-        const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
-        float zc = INFINITY;
-        if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
-            const int64_t cell = (int64_t)i * a.W + j;
-            const int32_t p = a.start[cell];
-            if (p < a.start[cell + 1]) zc = a.zs[p];
-        }
-        sEG[e] = -INFINITY;
-        sZC[e] = zc;
-        sOff[e] = 0;
-    }
-    float z_min = a.z_min;
-    if (a.zmin_from_data) {
-        z_min = key_float(a.zkeys[0]);
-        if (!isfinite(z_min)) z_min = 0.0f;
-    }
-
-    // ---- per-thread state of its strip: 8 cells in one column ----
-    const int half = warp % G::NHALF, strip = warp / G::NHALF;
-    const int ts = 32 * half + lane;           // tile column
-    const int tr0 = kStrip * strip;            // first tile row of the strip
-    const int j_out = tx0 + ts;
-    float cT[kStrip];
-    uint32_t run_lo = 0, run_hi = 0;           // run starts, one byte per cell
-    uint32_t validbits = 0, travbits = 0;
-    int wvalid = 0, wtrav = 0;
-#pragma unroll
-    for (int q = 0; q < kStrip; ++q) cT[q] = 0.0f;
-    auto run_get = [&](int q) -> int {
-        return q < 4 ? (run_lo >> (8 * q)) & 0xffu : (run_hi >> (8 * (q - 4))) & 0xffu;
-    };
-    auto run_set = [&](int q, int v) {
-        if (q < 4) run_lo = (run_lo & ~(0xffu << (8 * q))) | ((uint32_t)v << (8 * q));
-        else run_hi = (run_hi & ~(0xffu << (8 * (q - 4)))) | ((uint32_t)v << (8 * (q - 4)));
-    };
-    __syncthreads();
-
-    for (int k = 0; k < a.N; ++k) {
-        const bool first = k == 0;
-        const float h = __fmaf_rn((float)(k + 1), a.d_s, z_min);
-        uint32_t *sChgG = sChgG0 + (k & 1) * G::EH * G::EWW;
-        uint32_t *sChgC = sChgC0 + (k & 1) * G::EH * G::EWW;
-
-        // ---- 1. grounds and ceilings: advance the pointers past h ----
-        for (int e = tid; e < G::NE; e += kNT) {
-            float zc = sZC[e];
-            if (zc <= h) {
-                const int r = e / G::EW, s = e - r * G::EW;
-                const int64_t cell = (int64_t)(ty0 - G::HE + r) * a.W + (tx0 - G::HE + s);
-                const int32_t b = a.start[cell], end = a.start[cell + 1];
-                const float zg0 = sEG[e];
-                const uint32_t off = sOff[e];
-                int32_t p = off < kSat ? b + (int32_t)off : upper_bound(a.zs, b, end, zg0);
-                float zg;
-                do {
-                    zg = zc;
-                    ++p;
-                    zc = p < end ? a.zs[p] : INFINITY;
-                } while (zc <= h);
-                sEG[e] = zg;
-                sZC[e] = zc;
-                sOff[e] = (uint16_t)min((uint32_t)(p - b), kSat);
-                const uint32_t bit = 1u << (s & 31);
-                if (zg != zg0) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
-                atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
-            }
-        }
-        __syncthreads();
-
-        // the next slice's change words are cleared here, a barrier ahead of their use
-        {
-            uint32_t *nG = sChgG0 + ((k + 1) & 1) * G::EH * G::EWW;
-            uint32_t *nC = sChgC0 + ((k + 1) & 1) * G::EH * G::EWW;
-            for (int i = tid; i < G::EH * G::EWW; i += kNT) { nG[i] = 0; nC[i] = 0; }
-        }
-
-        // ---- 2. gentle flags (Eq. 2: m^grad < theta_s) ----
-#pragma unroll 1
-        for (int gr = warp; gr < G::GH; gr += kNW) {
-#pragma unroll
-            for (int w = 0; w < G::GPASS; ++w) {
-                // stencil rows gr..gr+2 of the elevation region, columns 32w..32w+33
-                uint32_t v = 0;
-                if (lane < 6) v = sChgG[(gr + (lane >> 1)) * G::EWW + w + (lane & 1)];
-                if (!first && !__any_sync(0xffffffffu, v != 0)) {
-                    if (lane == 0) sGChg[gr * G::GWW + w] = 0;
-                    continue;
-                }
-                const int gs = 32 * w + lane;
-                const int gsc = gs < G::GW ? gs : G::GW - 1;
-                const float *ep = sEG + (gr + 1) * G::EW + (gsc + 1);
-                const float e0 = ep[0], eL = ep[-1], eR = ep[1], eD = ep[-G::EW], eU = ep[G::EW];
-                const bool ok = e0 > -INFINITY && eL > -INFINITY && eR > -INFINITY &&
-                                eD > -INFINITY && eU > -INFINITY;
-                const float gx = (eR - eL) * c.inv2r;
-                const float gy = (eU - eD) * c.inv2r;
-                const bool gentle = ok && gx * gx + gy * gy < ts2 && gs < G::GW;
-                const uint32_t bits = __ballot_sync(0xffffffffu, gentle);
-                if (lane == 0) {
-                    const uint32_t old = sGB[gr * G::GWW + w];
-                    sGB[gr * G::GWW + w] = bits;
-                    sGChg[gr * G::GWW + w] = first ? 0xffffffffu : (bits ^ old);
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- the strip's ground and ceiling outputs and own changes ----
-        uint32_t gchbits = 0;
-#pragma unroll
-        for (int q = 0; q < kStrip; ++q) {
-            const int er = tr0 + q + G::HE, es = ts + G::HE;
-            const int i = ty0 + tr0 + q;
-            const float eg = sEG[er * G::EW + es];
-            if (i < a.H && j_out < a.W) {
-                const int64_t o = (int64_t)k * HW + (int64_t)i * a.W + j_out;
-                __stcs(&a.ground[o], eg);
-                __stcs(&a.ceil[o], sZC[er * G::EW + es]);
-            }
-            if (first || ((sChgG[er * G::EWW + (es >> 5)] >> (es & 31)) & 1u)) {
-                gchbits |= 1u << q;
-                if (eg > -INFINITY) validbits |= 1u << q;
-                else validbits &= ~(1u << q);
-            }
-        }
-
-        // ---- 3. interval (Eq. 1), terrain (Eq. 3-4), initial cost (Eq. 5) ----
-#pragma unroll 1
-        for (int cr = warp; cr < G::CH; cr += kNW) {
-#pragma unroll
-            for (int w = 0; w < G::CPASS; ++w) {
-                uint32_t v = 0;
-                if (lane < 6) v = sChgG[(cr + RP + (lane >> 1)) * G::EWW + w + (lane & 1)];
-                else if (lane < 8) v = sChgC[(cr + RP + 1) * G::EWW + w + (lane & 1)];
-                else if (lane < 8 + 2 * (2 * RP + 1))
-                    v = sGChg[(cr + ((lane - 8) >> 1)) * G::GWW + w + (lane & 1)];
-                if (!first && !__any_sync(0xffffffffu, v != 0)) {
-                    if (lane == 0) sCIChg[cr * G::CWW + w] = 0;
-                    continue;
-                }
-                const int cs = 32 * w + lane;
-                bool changed = false;
-                if (cs < G::CW) {
-                    const int i = ty0 - RK + cr, j = tx0 - RK + cs;
-                    float ci = 0.0f;                     // off-grid taps add nothing
-                    if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
-                        const int eidx = (cr + RP + 1) * G::EW + (cs + RP + 1);
-                        const float *ep = sEG + eidx;
-                        const float eg = ep[0];
-                        if (!(eg > -INFINITY)) {
-                            ci = c.c_b;
-                        } else {
-                            const float dI = sZC[eidx] - eg;
-                            float cI;
-                            if (dI < c.d_min) cI = c.c_b;
-                            else if (isinf(dI)) cI = 0.0f;
-                            else cI = fmaxf(0.0f, c.alpha_d * (c.d_ref - dI));
-                            const float eL = ep[-1], eR = ep[1], eD = ep[-G::EW], eU = ep[G::EW];
-                            float cg;
-                            if (!(eL > -INFINITY && eR > -INFINITY && eD > -INFINITY && eU > -INFINITY)) {
-                                cg = c.c_b;
-                            } else {
-                                const float gx = (eR - eL) * c.inv2r;
-                                const float gy = (eU - eD) * c.inv2r;
-                                const float m2 = gx * gx + gy * gy;
-                                const float mxy = fmaxf(fabsf(gx), fabsf(gy));
-                                if (mxy > c.theta_b) {
-                                    cg = c.c_b;
-                                } else if (m2 < ts2) {
-                                    cg = c.alpha_s * (m2 * inv_ts2);
-                                } else {
-                                    int count = 0;
-                                    const int w0 = cs >> 5, off = cs & 31;
-#pragma unroll
-                                    for (int dr = 0; dr <= 2 * RP; ++dr) {
-                                        const uint32_t *rowb = sGB + (cr + dr) * G::GWW;
-                                        const uint32_t bb = __funnelshift_r(rowb[w0], rowb[w0 + 1], off);
-                                        count += __popc(bb & ((1u << (2 * RP + 1)) - 1u));
-                                    }
-                                    const int cc = cs + RP;
-                                    count -= (sGB[(cr + RP) * G::GWW + (cc >> 5)] >> (cc & 31)) & 1u;
-                                    const float t = mxy * c.inv_tb;
-                                    cg = count > c.count_thresh ? c.alpha_b * (t * t) : c.c_b;
-                                }
-                            }
-                            ci = fminf(c.c_b, cI + cg);
-                        }
-                    }
-                    const int cidx = cr * G::CW + cs;
-                    changed = first || __float_as_uint(ci) != __float_as_uint(sCI[cidx]);
-                    sCI[cidx] = ci;
-                }
-                const uint32_t cbits = __ballot_sync(0xffffffffu, changed);
-                if (lane == 0) sCIChg[cr * G::CWW + w] = cbits;
-            }
-        }
-        __syncthreads();
-
-        // ---- 4. inflation (Eq. 6) of the strip, uniqueness, outputs ----
-        uint32_t v = 0;
-        for (int x = lane; x < 2 * (kStrip + 2 * RK); x += 32)
-            v |= sCIChg[(tr0 + (x >> 1)) * G::CWW + half + (x & 1)];
-        const bool need_infl = __any_sync(0xffffffffu, v != 0);
-        const bool need_simp = need_infl || __any_sync(0xffffffffu, gchbits != 0);
-        if (need_simp) {
-            float acc[kStrip];
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) acc[q] = cT[q];
-            if (need_infl) {
-#pragma unroll
-                for (int q = 0; q < kStrip; ++q) acc[q] = 0.0f;
-#pragma unroll
-                for (int rr = 0; rr < kStrip + 2 * RK; ++rr) {
-                    const float *row = sCI + (tr0 + rr) * G::CW + ts;
-                    float P[RK + 1];
-                    P[0] = row[RK];
-#pragma unroll
-                    for (int d = 1; d <= RK; ++d) P[d] = fmaxf(row[RK - d], row[RK + d]);
-#pragma unroll
-                    for (int q = 0; q < kStrip; ++q) {
-                        const int n = rr - RK - q;       // row offset of this row for cell q
-                        if (n < -RK || n > RK) continue;
-                        const int an = n < 0 ? -n : n;
-                        const float *Kr = c.K + (an + RK) * (2 * RK + 1) + RK;
-                        // the disc d^2 < (RK+1)^2 holds every positive weight
-#pragma unroll
-                        for (int d = 0; d <= RK; d += 2) {
-                            if (d * d + an * an >= (RK + 1) * (RK + 1)) break;
-                            const float t0 = Kr[d] * P[d];
-                            const float t1 = (d + 1 <= RK && (d + 1) * (d + 1) + an * an < (RK + 1) * (RK + 1))
-                                                 ? Kr[d + 1] * P[d + 1] : 0.0f;
-                            acc[q] = max3(acc[q], t0, t1);
-                        }
-                    }
-                }
-            }
-            // Eq. 9 of slice k-1 against slice k, then the rows p it is unique against
-            int pre = 0;
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const int i = ty0 + tr0 + q;
-                const bool gq = (gchbits >> q) & 1u;
-                if (!first && i < a.H && j_out < a.W && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
-                    const int kk = k - 1, r0 = run_get(q);
-                    const int64_t cell = (int64_t)i * a.W + j_out;
-                    for (int p = r0; p < kk; ++p) {
-                        const float cp = a.cost[(int64_t)p * HW + cell];
-                        if (cT[q] < cp) atomicOr(&a.ubits[4 * kk + ((p + 1) >> 5)], 1u << ((p + 1) & 31));
-                    }
-                    pre = max(pre, r0 + 1);
-                }
-                if (gq) run_set(q, k);
-                cT[q] = acc[q];
-            }
-            const int wmax = __reduce_max_sync(0xffffffffu, pre);
-            if (lane == 0 && wmax > 0) atomicMax(&s_upre[k - 1], wmax);
-            travbits = 0;
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q)
-                if (cT[q] < c.c_b) travbits |= 1u << q;
-            int nv = 0, nt = 0;
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const bool in_map = ty0 + tr0 + q < a.H && j_out < a.W;
-                nv += __popc(__ballot_sync(0xffffffffu, in_map && ((validbits >> q) & 1u)));
-                nt += __popc(__ballot_sync(0xffffffffu, in_map && ((travbits >> q) & 1u)));
-            }
-            wvalid = nv;
-            wtrav = nt;
-        }
-        if (lane == 0) {
-            if (wvalid) atomicAdd(&s_valid[k], wvalid);
-            if (wtrav) atomicAdd(&s_trav[k], wtrav);
-        }
-        if (j_out < a.W) {
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const int i = ty0 + tr0 + q;
-                if (i < a.H) {
-                    const int64_t o = (int64_t)k * HW + (int64_t)i * a.W + j_out;
-                    __stcs(&a.cost[o], cT[q]);
-                    a.mask[o] = (travbits >> q) & 1u;
-                }
-            }
-        }
-    }
-
-    // Eq. 9 holds vacuously for the last slice
-    {
-        int pre = 0;
-#pragma unroll
-        for (int q = 0; q < kStrip; ++q) {
-            const int i = ty0 + tr0 + q;
-            if (i < a.H && j_out < a.W && cT[q] < c.c_b) {
-                const int kk = a.N - 1, r0 = run_get(q);
-                const int64_t cell = (int64_t)i * a.W + j_out;
-                for (int p = r0; p < kk; ++p) {
-                    const float cp = a.cost[(int64_t)p * HW + cell];
-                    if (cT[q] < cp) atomicOr(&a.ubits[4 * kk + ((p + 1) >> 5)], 1u << ((p + 1) & 31));
-                }
-                pre = max(pre, r0 + 1);
-            }
-        }
-        const int wmax = __reduce_max_sync(0xffffffffu, pre);
-        if (lane == 0 && wmax > 0) atomicMax(&s_upre[a.N - 1], wmax);
-    }
-    __syncthreads();
-    for (int k = tid; k < a.N; k += kNT) {
-        if (s_upre[k]) atomicMax(&a.upre[k], s_upre[k]);
-        if (s_valid[k])
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats->valid_cells[k]),
-                      (unsigned long long)s_valid[k]);
-        if (s_trav[k])
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats->trav_cells[k]),
-                      (unsigned long long)s_trav[k]);
-    }
-}
-
-// Resident CTAs per SM that the tile's shared memory and 64 registers per
-// thread allow.
-template <int RK, int RP, int TW, int TH>
-struct Occupancy {
-    using G = Geo<RK, RP, TW, TH>;
-    static constexpr int by_smem = (int)(200000 / (G::smem_bytes() + 2048));
-    static constexpr int by_regs = 65536 / (64 * G::NT);
-    static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
-};
-
-template <int RK, int RP, int TW, int TH>
-__global__ void __launch_bounds__(Geo<RK, RP, TW, TH>::NT, (Occupancy<RK, RP, TW, TH>::value))
-k_stack_inc(const __grid_constant__ IncArgs args) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ SliceCounters counters;
-    stack_tile<RK, RP, TW, TH>(args.m, args.c, blockIdx.x * TW, blockIdx.y * TH, smem, counters);
-}
-
-template <int RK, int RP, int TW, int TH>
-cudaError_t run_inc(const IncArgs &a, cudaStream_t s) {
-    using G = Geo<RK, RP, TW, TH>;
-    const size_t smem = G::smem_bytes();
-    auto fn = k_stack_inc<RK, RP, TW, TH>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.m.W + TW - 1) / TW, (a.m.H + TH - 1) / TH);
-    fn<<<grid, G::NT, smem, s>>>(a);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- batches
-//
-// One persistent launch over the tiles of many maps: each CTA takes the next
-// (map, tile) item from a queue; maps come largest first so the long tiles
-// start early.  The descriptors travel in the kernel parameters.
-
-struct BatchArgs {
-    EvalConsts c;
-    int32_t n_maps;
-    int32_t total;                       // items
-    int32_t *queue;                      // next item (zero before the launch)
-    int32_t item_start[TCT_MAX_BATCH + 1];
-    int32_t tiles_x[TCT_MAX_BATCH];
-    IncMap maps[TCT_MAX_BATCH];
-};
-
-template <int RK, int RP, int TW, int TH>
-__global__ void __launch_bounds__(Geo<RK, RP, TW, TH>::NT, (Occupancy<RK, RP, TW, TH>::value))
-k_stack_batched(const __grid_constant__ BatchArgs b) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ SliceCounters counters;
-    __shared__ int32_t s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(b.queue, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= b.total) break;
-        int m = 0;
-        while (m + 1 < b.n_maps && b.item_start[m + 1] <= item) ++m;
-        const int t = item - b.item_start[m];
-        const int tx = t % b.tiles_x[m], ty = t / b.tiles_x[m];
-        stack_tile<RK, RP, TW, TH>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
-        __syncthreads();
-    }
-}
-
-template <int RK, int RP, int TW, int TH>
-cudaError_t run_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
-    using G = Geo<RK, RP, TW, TH>;
-    const size_t smem = G::smem_bytes();
-    auto fn = k_stack_batched<RK, RP, TW, TH>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148, fit = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, G::NT, smem);
-    if (e != cudaSuccess) return e;
-    if (fit < 1) fit = 1;
-    int per_sm = ctas_per_sm > 0 && ctas_per_sm < fit ? ctas_per_sm : fit;
-    int grid = sms * per_sm;
-    if (grid > b.total) grid = b.total > 0 ? b.total : 1;
-    fn<<<grid, G::NT, smem, s>>>(b);
-    count_launches(1);
-    return cudaGetLastError();
-}
+using inc::BatchArgs;
+using inc::IncMap;
 
 IncMap inc_map(const StackArgs &a) {
     IncMap m;
@@ -546,21 +18,11 @@ IncMap inc_map(const StackArgs &a) {
     return m;
 }
 
-template <int TW, int TH>
-cudaError_t dispatch_single(const IncArgs &a, cudaStream_t s) {
-    const int RK = a.c.rk, RP = a.c.patch_radius;
-    if (RP == 2 && RK == 5) return run_inc<5, 2, TW, TH>(a, s);
-    if (RP == 2 && RK == 4) return run_inc<4, 2, TW, TH>(a, s);
-    if (RP == 2 && RK == 12) return run_inc<12, 2, TW, TH>(a, s);
-    return cudaErrorNotSupported;
-}
-
-template <int TW, int TH>
-cudaError_t dispatch_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
+cudaError_t dispatch(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t s) {
     const int RK = b.c.rk, RP = b.c.patch_radius;
-    if (RP == 2 && RK == 5) return run_batched<5, 2, TW, TH>(b, ctas_per_sm, s);
-    if (RP == 2 && RK == 4) return run_batched<4, 2, TW, TH>(b, ctas_per_sm, s);
-    if (RP == 2 && RK == 12) return run_batched<12, 2, TW, TH>(b, ctas_per_sm, s);
+    if (RP == 2 && RK == 5) return inc::run_r5(b, tile, ctas_per_sm, s);
+    if (RP == 2 && RK == 4) return inc::run_r4(b, tile, ctas_per_sm, s);
+    if (RP == 2 && RK == 12) return inc::run_r12(b, tile, ctas_per_sm, s);
     return cudaErrorNotSupported;
 }
 
@@ -572,13 +34,8 @@ bool inc_supported(const EvalConsts &c, int n_slices) {
     return RP == 2 && (RK == 5 || RK == 4 || RK == 12);
 }
 
-cudaError_t launch_stack_inc(const StackArgs &a, int tile, cudaStream_t s) {
-    if (!inc_supported(a.c, a.N)) return cudaErrorNotSupported;
-    IncArgs args;
-    args.m = inc_map(a);
-    args.c = a.c;
-    if (tile == TCT_TILE_32) return dispatch_single<32, 32>(args, s);
-    return dispatch_single<64, 64>(args, s);
+cudaError_t launch_stack_inc(const StackArgs &a, int32_t *queue, int tile, cudaStream_t s) {
+    return launch_stack_batched(a.c, 1, &a, queue, tile, 0, s);
 }
 
 cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,
@@ -600,8 +57,7 @@ cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArg
     }
     b.item_start[n_maps] = total;
     b.total = total;
-    if (tile == TCT_TILE_32) return dispatch_batched<32, 32>(b, ctas_per_sm, s);
-    return dispatch_batched<64, 64>(b, ctas_per_sm, s);
+    return dispatch(b, tile, ctas_per_sm, s);
 }
 
 }  // namespace tct
