@@ -147,7 +147,7 @@ def stack_traffic():
     or None when the kernel source changed since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_stack_inc_parking.txt")
-    src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cu")
+    src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cuh")
     try:
         rec = {}
         with open(path) as f:
@@ -162,6 +162,24 @@ def stack_traffic():
         return int(rec["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def max_over_ranks(ms: float, device) -> float:
+    """The step time of the whole job: the slowest rank's (a collective for timing
+    only; the ranks exchange no data)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank builds its
+    own replica of the workload, so the job processes world x units per step."""
+    return units_per_rank * world / (ms * 1e-3) / 1e6
 
 
 def dist_env():
@@ -183,6 +201,69 @@ def cpu_baseline(sc, params):
     return {"value": len(sc.points) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": round(dt, 3),
             "sample": "the full workload once (build, evaluate with fragility bounds, chain)"}
+
+
+def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps):
+    """256 paths x 512 waypoints on the evaluated tomogram: straight lines between
+    random traversable cells of the most traversable kept slice plus N(0, 0.2 m)
+    noise.  Times the query + adjoint kernels and the 50-step fused refinement."""
+    import torch
+    from paper_2403_07631_gb300 import tct
+    st = tct.stats_from(stats)
+    g = tct.Grid(grid.x0, grid.y0, grid.res, grid.W, grid.H, grid.d_s, grid.n_slices,
+                 float(st.z_min), True)
+    k = int(max(range(grid.n_slices), key=lambda i: st.trav_cells[i]))
+    gen = torch.Generator(device="cpu").manual_seed(4)
+    cells = torch.nonzero(mask[k].cpu().reshape(-1)).reshape(-1)
+    paths, L = 256, 512
+    pick = cells[torch.randint(len(cells), (paths, 2), generator=gen)]
+    ij = torch.stack([pick // grid.W, pick % grid.W], -1).double()          # [paths, 2, (i, j)]
+    ends = torch.stack([grid.x0 + (ij[..., 1] + 0.5) * grid.res,
+                        grid.y0 + (ij[..., 0] + 0.5) * grid.res], -1)       # [paths, 2, (x, y)]
+    t = torch.linspace(0, 1, L, dtype=torch.float64)[None, :, None]
+    xy = ends[:, :1] * (1 - t) + ends[:, 1:] * t
+    xy[:, 1:-1] += 0.2 * torch.randn(paths, L - 2, 2, generator=gen, dtype=torch.float64)
+    xy = xy.float().contiguous().to(dev)
+    sl = torch.full((paths, L), k, dtype=torch.int32, device=dev)
+    q = paths * L
+    c_out = torch.empty(paths, L, device=dev)
+    e_out = torch.empty(paths, L, device=dev)
+    gxy = torch.empty_like(xy)
+    ones = torch.ones(paths, L, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd_bwd():
+        tct.tct_sample_cost(g, cost, ground, xy, sl, c_out, e_out)
+        tct.tct_sample_cost_backward(g, cost, ground, xy, sl, ones, None, gxy)
+
+    def timed(fn, n):
+        out = []
+        for i in range(n + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if i >= 3:
+                out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    t_fb = timed(fwd_bwd, max(steps, 10))
+    tct.tct_sample_cost(g, cost, None, xy, sl, c_out, None)
+    before = float(c_out.mean())
+    work = xy.clone()
+
+    def refine():
+        work.copy_(xy)
+        tct.tct_refine_paths(g, cost, sl, work, 50, 1e-3, 1.0)
+
+    t_ref = timed(refine, max(steps, 5))
+    tct.tct_sample_cost(g, cost, None, work, sl, c_out, None)
+    after = float(c_out.mean())
+    return {"workload": "256 paths x 512 waypoints on slice %d of the parking structure" % k,
+            "query_fwd_bwd_ms": t_fb, "waypoints_per_s_fwd_bwd": q / (t_fb * 1e-3),
+            "refine_50_steps_ms": t_ref, "waypoint_steps_per_s": 50 * q / (t_ref * 1e-3),
+            "mean_cost_before": before, "mean_cost_after": after}
 
 
 def batched_vs_plain(dev, params, steps):
@@ -341,10 +422,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     stack_ms = statistics.mean(p[1] for p in phase)
     part_ms = statistics.mean(p[0] for p in phase)
     chain_ms = statistics.mean(p[2] for p in phase)
@@ -373,7 +451,7 @@ def main():
     st = tct.stats_from(stats)
     peak, peak_src = measured_peak_gbs()
     units = P * world
-    value = units / (ms * 1e-3) / 1e6
+    value = job_value(P, world, ms)
     path_gbs = algorithmic_bytes(P, N, H, W) / (ms * 1e-3) / 1e9
     sb = stack_bytes(P, N, H, W)
     stack_gbs = sb / (stack_ms * 1e-3) / 1e9
@@ -398,6 +476,7 @@ def main():
         "clocks": clocks,
         "kept_slices": int(st.n_kept),
     }
+    out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
     if not args.no_batched:
         del ws, ground, ceil, cost, mask, keep
         torch.cuda.empty_cache()
