@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-map batched-versus-plain measurement")
+    ap.add_argument("--no-stress", action="store_true",
+                    help="skip the 60M-point cave-terrain measurement")
     return ap.parse_args()
 
 
@@ -187,26 +189,33 @@ def dist_env():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def cpu_baseline(sc, params):
-    """The FP64 oracle as it stands, on the same workload, on the host cores."""
+def cpu_baseline(sc, params, min_seconds=10.0, max_runs=20):
+    """The FP64 oracle as it stands, on the same workload, on the host cores:
+    whole runs (build, evaluate with fragility bounds, chain) repeated until
+    `min_seconds` have passed; the value is the mean over the runs."""
     import oracle
     oracle.compile_library()
     op = {k: params[k] for k in oracle.PARAM_FIELDS}
-    g = oracle.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, 0.0, sc.n_slices)
-    t0 = time.perf_counter()
-    eG, eC, g, _, _ = oracle.build(sc.points, g, True)
-    cT, mask, frag = oracle.evaluate(g, op, eG, eC)
-    oracle.simplify(eG, cT, op["c_b"], frag)
-    dt = time.perf_counter() - t0
+    runs = []
+    while len(runs) < max_runs and sum(runs) < min_seconds:
+        g = oracle.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, 0.0, sc.n_slices)
+        t0 = time.perf_counter()
+        eG, eC, g, _, _ = oracle.build(sc.points, g, True)
+        cT, mask, frag = oracle.evaluate(g, op, eG, eC)
+        oracle.simplify(eG, cT, op["c_b"], frag)
+        runs.append(time.perf_counter() - t0)
+    dt = statistics.mean(runs)
     return {"value": len(sc.points) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "seconds": round(dt, 3),
-            "sample": "the full workload once (build, evaluate with fragility bounds, chain)"}
+            "kind": "oracle", "seconds": round(dt, 3), "runs": len(runs),
+            "sample": "%d whole runs of the workload (build, evaluate with fragility bounds, "
+                      "chain), mean time per run" % len(runs)}
 
 
-def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps):
-    """256 paths x 512 waypoints on the evaluated tomogram: straight lines between
+def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps, paths=256, L=512,
+                  refine_steps=50, label="the parking structure"):
+    """`paths` x `L` waypoints on the evaluated tomogram: straight lines between
     random traversable cells of the most traversable kept slice plus N(0, 0.2 m)
-    noise.  Times the query + adjoint kernels and the 50-step fused refinement."""
+    noise.  Times the query + adjoint kernels and the fused refinement."""
     import torch
     from paper_2403_07631_gb300 import tct
     st = tct.stats_from(stats)
@@ -214,8 +223,7 @@ def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps):
                  float(st.z_min), True)
     k = int(max(range(grid.n_slices), key=lambda i: st.trav_cells[i]))
     gen = torch.Generator(device="cpu").manual_seed(4)
-    cells = torch.nonzero(mask[k].cpu().reshape(-1)).reshape(-1)
-    paths, L = 256, 512
+    cells = torch.nonzero(mask[k].reshape(-1)).reshape(-1).cpu()
     pick = cells[torch.randint(len(cells), (paths, 2), generator=gen)]
     ij = torch.stack([pick // grid.W, pick % grid.W], -1).double()          # [paths, 2, (i, j)]
     ends = torch.stack([grid.x0 + (ij[..., 1] + 0.5) * grid.res,
@@ -249,21 +257,23 @@ def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps):
         return statistics.median(out)
 
     t_fb = timed(fwd_bwd, max(steps, 10))
-    tct.tct_sample_cost(g, cost, None, xy, sl, c_out, None)
-    before = float(c_out.mean())
-    work = xy.clone()
+    out = {"workload": "%d paths x %d waypoints on slice %d of %s" % (paths, L, k, label),
+           "query_fwd_bwd_ms": t_fb, "waypoints_per_s_fwd_bwd": q / (t_fb * 1e-3)}
+    if refine_steps:
+        tct.tct_sample_cost(g, cost, None, xy, sl, c_out, None)
+        before = float(c_out.mean())
+        work = xy.clone()
 
-    def refine():
-        work.copy_(xy)
-        tct.tct_refine_paths(g, cost, sl, work, 50, 1e-3, 1.0)
+        def refine():
+            work.copy_(xy)
+            tct.tct_refine_paths(g, cost, sl, work, refine_steps, 1e-3, 1.0)
 
-    t_ref = timed(refine, max(steps, 5))
-    tct.tct_sample_cost(g, cost, None, work, sl, c_out, None)
-    after = float(c_out.mean())
-    return {"workload": "256 paths x 512 waypoints on slice %d of the parking structure" % k,
-            "query_fwd_bwd_ms": t_fb, "waypoints_per_s_fwd_bwd": q / (t_fb * 1e-3),
-            "refine_50_steps_ms": t_ref, "waypoint_steps_per_s": 50 * q / (t_ref * 1e-3),
-            "mean_cost_before": before, "mean_cost_after": after}
+        t_ref = timed(refine, max(steps, 5))
+        tct.tct_sample_cost(g, cost, None, work, sl, c_out, None)
+        out.update({"refine_%d_steps_ms" % refine_steps: t_ref,
+                    "waypoint_steps_per_s": refine_steps * q / (t_ref * 1e-3),
+                    "mean_cost_before": before, "mean_cost_after": float(c_out.mean())})
+    return out
 
 
 def batched_vs_plain(dev, params, steps):
@@ -331,6 +341,53 @@ def batched_vs_plain(dev, params, steps):
                        "points_per_block": tuning.points_per_block}}
 
 
+def stress(dev, params, steps):
+    """Cave terrain: 60M points over 200 x 200 x 40 m, 4000 x 4000 cells at
+    0.05 m (inflation radius 12 cells), 80 slices; one build + evaluate per
+    step (inputs resident, L2 flushed before each), then 4096 paths x 512
+    waypoints queried forward and backward on the result."""
+    import torch
+    from paper_2403_07631_gb300 import scenes, tct
+    sc = scenes.cave_terrain()
+    P, N, H, W = len(sc.points), sc.n_slices, sc.H, sc.W
+    grid = tct.Grid(sc.x0, sc.y0, sc.res, W, H, sc.d_s, N, 0.0, True)
+    pts = torch.from_numpy(sc.points).to(dev)
+    del sc.points
+    ws, ground, ceil, cost, mask, keep, stats = tct.alloc_outputs(grid, P, dev, params)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    times, phase = [], []
+    for i in range(steps + 2):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tct.tct_build_evaluate(pts, grid, params, ws, ground, ceil, cost, mask, keep, stats)
+        b.record(stream)
+        ph = tct.tct_timing_read()
+        b.synchronize()
+        if i >= 2:
+            times.append(a.elapsed_time(b))
+            phase.append(ph)
+    ms = statistics.median(times)
+    st = tct.stats_from(stats)
+    peak = measured_peak_gbs()[0]
+    del ws, ceil, pts
+    torch.cuda.empty_cache()
+    q = sampler_paths(dev, grid, params, cost, ground, mask, stats, steps, paths=4096, L=512,
+                      refine_steps=0, label="the cave terrain")
+    stack_ms = statistics.median(p[1] for p in phase)
+    return {"workload": sc.name, "points": P, "grid": [H, W], "res_m": sc.res, "slices": N,
+            "ms_per_step": ms, "mpoints_per_s": P / (ms * 1e-3) / 1e6,
+            "slice_cells_per_s": N * H * W / (ms * 1e-3),
+            "path_roofline_frac": algorithmic_bytes(P, N, H, W) / (ms * 1e-3) / 1e9 / peak,
+            "phases_ms": {"partition": statistics.median(p[0] for p in phase),
+                          "stack": stack_ms, "chain": statistics.median(p[2] for p in phase)},
+            "stack_roofline_frac": stack_bytes(P, N, H, W) / (stack_ms * 1e-3) / 1e9 / peak,
+            "kept_slices": int(st.n_kept), "dropped_points": int(st.n_dropped),
+            "valid_cells": int(sum(st.valid_cells[:N])), "trav_cells": int(sum(st.trav_cells[:N])),
+            "queries": q}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -347,7 +404,7 @@ def run_reference(args):
     sc = workload(args.workload)
     times = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(sc, tct_params)
+        cb = cpu_baseline(sc, tct_params, min_seconds=0.0, max_runs=1)
         if i >= args.warmup:
             times.append(cb["seconds"])
     t = statistics.mean(times)
@@ -481,6 +538,12 @@ def main():
         del ws, ground, ceil, cost, mask, keep
         torch.cuda.empty_cache()
         out["batched_vs_plain"] = batched_vs_plain(dev, params, min(args.steps, 5))
+        torch.cuda.empty_cache()
+    if not args.no_stress:
+        if args.no_batched:
+            del ws, ground, ceil, cost, mask, keep
+            torch.cuda.empty_cache()
+        out["stress"] = stress(dev, params, min(args.steps, 3))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, params)
     if world > 1:

@@ -317,3 +317,102 @@ def batched_maps(seed_base: int = 3000, count: int = 64, p_lo: int = 50_000,
         sc.n_slices = n_sl
         out.append(sc)
     return out
+
+
+# ------------------------------------------------------------- cave terrain
+
+def _value_noise(rng, x, y, spacing, extent):
+    """Smooth noise in [-1, 1]: random values on a lattice `spacing` apart,
+    interpolated with a smoothstep."""
+    n = int(math.ceil(extent / spacing)) + 2
+    lat = rng.uniform(-1.0, 1.0, (n, n))
+    u, v = x / spacing, y / spacing
+    i0 = np.clip(np.floor(v).astype(np.int64), 0, n - 2)
+    j0 = np.clip(np.floor(u).astype(np.int64), 0, n - 2)
+    fu, fv = u - j0, v - i0
+    su, sv = fu * fu * (3 - 2 * fu), fv * fv * (3 - 2 * fv)
+    a = lat[i0, j0] * (1 - su) + lat[i0, j0 + 1] * su
+    b = lat[i0 + 1, j0] * (1 - su) + lat[i0 + 1, j0 + 1] * su
+    return a * (1 - sv) + b * sv
+
+
+def _fractal(seed, x, y, extent, amplitude, octaves=5, base=50.0):
+    rng = np.random.default_rng(seed)
+    z = np.zeros_like(x)
+    amp, spacing, total = 1.0, base, 0.0
+    for _ in range(octaves):
+        z += amp * _value_noise(rng, x, y, spacing, extent)
+        total += amp
+        amp *= 0.5
+        spacing *= 0.5
+    return amplitude * z / total
+
+
+def cave_terrain(seed: int = 5, n_points: int = 60_000_000, side_cells: int = 4000,
+                 res: float = 0.05, n_tunnels: int = 30, n_shelves: int = 2000) -> Scene:
+    """Multi-layer terrain over 200 x 200 x 40 m: fractal value-noise ground
+    (5 octaves, amplitude 6 m) sampled once per 0.05 m cell, cave tunnels
+    beneath it as noise-perturbed tubes of radius 2-4 m, and overhanging rock
+    shelves 1-3.5 m above the ground; grid 4000 x 4000 at 0.05 m, 80 slices."""
+    rng = np.random.default_rng(seed)
+    L = side_cells * res
+    sigma = 0.02
+
+    def ground(x, y):
+        return 20.0 + _fractal(seed, x, y, L, 6.0)
+
+    parts = [_strat_rect(rng, 0.0, 0.0, side_cells, side_cells, res, ground, sigma)]
+    n_ground = len(parts[0])
+    # shelves: horizontal undersides above the local ground
+    shelf_area = []
+    shelves = []
+    for _ in range(n_shelves):
+        sx, sy = rng.uniform(1.0, 4.0), rng.uniform(0.5, 2.0)
+        x0, y0 = rng.uniform(0, L - sx), rng.uniform(0, L - sy)
+        z = float(ground(np.array([x0 + sx / 2]), np.array([y0 + sy / 2]))[0]) + rng.uniform(1.0, 3.5)
+        shelves.append((x0, y0, sx, sy, z))
+        shelf_area.append(sx * sy)
+    n_shelf_pts = int(min(4_000_000, 0.07 * n_points))
+    per = rng.multinomial(n_shelf_pts, np.array(shelf_area) / np.sum(shelf_area))
+    for (x0, y0, sx, sy, z), m in zip(shelves, per):
+        parts.append(_rand_rect_h(rng, m, x0, y0, sx, sy, z, sigma))
+    # tunnels: tubes along noise-perturbed paths 6-10 m below the ground, as
+    # long as 0.5-1.25 map sides (100-250 m on the 200 m map)
+    n_tun_pts = max(0, n_points - n_ground - n_shelf_pts)
+    lengths = rng.uniform(0.5 * L, 1.25 * L, n_tunnels)
+    radii = rng.uniform(2.0, 4.0, n_tunnels)
+    area = 2 * math.pi * radii * lengths
+    per = rng.multinomial(n_tun_pts, area / area.sum())
+    tunnel_points = []
+    for t in range(n_tunnels):
+        m = int(per[t])
+        if m == 0:
+            continue
+        sx, sy = rng.uniform(0.05 * L, 0.95 * L, 2)
+        head = rng.uniform(0, 2 * math.pi)
+        depth = rng.uniform(6.0, 10.0)
+        # centre line sampled every 0.5 m with a slowly wandering heading
+        ns = int(lengths[t] / 0.5) + 1
+        turn = np.cumsum(rng.normal(0.0, 0.05, ns))
+        hx, hy = np.cos(head + turn), np.sin(head + turn)
+        cx = np.clip(sx + np.cumsum(hx) * 0.5, 1.0, L - 1.0)
+        cy = np.clip(sy + np.cumsum(hy) * 0.5, 1.0, L - 1.0)
+        cz = ground(cx, cy) - depth
+        tunnel_points.append((float(cx[ns // 2]), float(cy[ns // 2])))
+        k = rng.integers(0, ns, m)
+        phi = rng.uniform(0.0, 2 * math.pi, m)
+        r = radii[t] * (1.0 + 0.15 * rng.uniform(-1.0, 1.0, m))
+        nx, ny = -hy[k], hx[k]
+        x = cx[k] + r * np.cos(phi) * nx
+        y = cy[k] + r * np.cos(phi) * ny
+        z = cz[k] + r * np.sin(phi) + rng.normal(0.0, sigma, m)
+        parts.append(np.stack([x, y, z], 1).astype(np.float32))
+
+    def topup(m):
+        return _rand_rect_h(rng, m, 0.0, 0.0, L, L, ground, sigma)
+
+    pts = _finish(rng, [p.astype(np.float32) for p in parts], n_points, topup)
+    return Scene(f"cave terrain {n_points / 1e6:g}M pts, {side_cells}x{side_cells} @{res:g} m, 80 slices",
+                 pts, 0.0, 0.0, res, side_cells, side_cells, 0.5, 80,
+                 dict(seed=seed, n_tunnels=n_tunnels, n_shelves=n_shelves,
+                      tunnel_points=tunnel_points))
