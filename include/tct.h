@@ -302,6 +302,49 @@ int tct_build_evaluate_noalloc(const float *d_xyz, int64_t n, int32_t stride,
                                float *d_ceil, float *d_cost, uint8_t *d_mask, uint8_t *d_keep,
                                tct_stats *d_stats, tct_stream stream);
 
+/* ---- path search across slices (Sec. III-D), a host stage -------------- */
+
+/*
+ * A planner over an evaluated tomogram in HOST memory: h_ground and h_cost
+ * are the [N][H][W] e^G and c^T layers (grid->n_slices = N), h_keep the keep
+ * flags (NULL: every slice).  The planner reads the caller's arrays in place
+ * (no copy): they must stay alive and unchanged until tct_planner_destroy.
+ * Only grid->H, W, n_slices and res are used; c_b is the barrier cost c^B.
+ *
+ * The graph is that of Sec. III-D on the kept slices: a state is a cell on
+ * one kept slice and connects to its 8 neighbours on that slice; cells of
+ * adjacent kept slices with equal ground are one node, whose cost c^N is
+ * the minimum of their c^T; moving onto a node costs c^N plus the Euclidean
+ * distance between the nodes in cell units (elevation change / res); nodes
+ * with c^N >= c^B cannot be entered; a gateway moves at no cost to the same
+ * node on the adjacent kept slice where c^T is lower.  Search: A* with the
+ * octile distance to the goal cell as heuristic (optimal path costs).
+ * Returns TCT_ERR_INVALID_ARG for a bad grid, NULL arrays or no kept slice.
+ */
+typedef struct tct_planner tct_planner;
+int tct_planner_create(const tct_grid *grid, const float *h_ground, const float *h_cost,
+                       const uint8_t *h_keep, float c_b, tct_planner **out);
+void tct_planner_destroy(tct_planner *planner);
+
+/*
+ * Plans n_queries paths, in parallel on n_threads host threads (<= 0: one
+ * per hardware thread).  h_starts / h_goals: [n][3] int32 (i, j, slice); the
+ * slice is an original index and must be kept, else TCT_ERR_INVALID_ARG
+ * (nothing planned).  Outputs, all host arrays: h_paths [n][max_len][3] the
+ * states (i, j, slice) from start to goal, a gateway appearing as two
+ * consecutive states of the same cell; h_lens [n] the number of states
+ * (0 when the goal cannot be reached or an end point lies on a node with
+ * c^N >= c^B); h_costs [n] the path cost (+inf when unreachable);
+ * h_expanded [n] states expanded (may be NULL).  A path longer than max_len
+ * is cut to its first max_len states, its full length still goes to h_lens,
+ * and the call returns TCT_ERR_WORKSPACE_TOO_SMALL.  Each thread holds
+ * about 13 bytes per (kept slice, cell) of search state, kept in the
+ * planner for later calls.  Calls on one planner may run concurrently.
+ */
+int tct_plan_paths(tct_planner *planner, int32_t n_queries, const int32_t *h_starts,
+                   const int32_t *h_goals, int32_t max_len, int32_t *h_paths, int32_t *h_lens,
+                   double *h_costs, int64_t *h_expanded, int32_t n_threads);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /*

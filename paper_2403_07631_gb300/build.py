@@ -1,6 +1,7 @@
 """Builds libtct.so (the CUDA kernels and the C ABI) in-tree for sm_103a.
 
-Each .cu file under csrc/ is compiled by nvcc in parallel, then linked into
+Each .cu file under csrc/ is compiled by nvcc (each .cpp file, host-only
+code, by the host C++ compiler) in parallel, then linked into
 _build/libtct.so with the CUDA runtime linked statically, so the library
 loads on a machine without a GPU (calls then fail with TCT_ERR_CUDA).
 """
@@ -32,7 +33,14 @@ def nvcc() -> str:
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def gxx() -> str:
+    for cand in (os.environ.get("CXX"), shutil.which("g++"), shutil.which("c++")):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("no C++ compiler found for the host stages of libtct")
 
 
 def _deps():
@@ -55,13 +63,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *CFLAGS, "-c", src, "-o", obj]
-        if verbose:
-            cmd += ["-Xptxas", "-v"]
+        obj = os.path.join(OUT, os.path.splitext(os.path.basename(src))[0] + ".o")
+        if src.endswith(".cpp"):
+            # host-only code: the host compiler directly
+            cmd = [gxx(), "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", CSRC,
+                   "-c", src, "-o", obj]
+        else:
+            cmd = [cc, *ARCH, *CFLAGS, "-c", src, "-o", obj]
+            if verbose:
+                cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+            raise RuntimeError(f"compiler failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
@@ -70,7 +83,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             print(log)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static",
+           "-Xcompiler", "-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -109,6 +109,11 @@ _SIGNATURES = {
     "tct_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
+    "tct_planner_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "tct_planner_destroy": (None, [_P]),
+    "tct_plan_paths": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P, _P,
+                                      ctypes.c_int32]),
 }
 
 _lib = None
@@ -459,3 +464,56 @@ def tct_timing_read() -> list[float]:
 
 def tct_launch_count() -> int:
     return int(load().tct_launch_count())
+
+
+class Planner:
+    """Path search across the kept slices (tct_planner_*, a host stage of the
+    library): ground / cost are host numpy [N, H, W] float32 layers, keep
+    the [N] keep flags (None: all slices).  The arrays are held for the
+    planner's lifetime; the library reads them in place."""
+
+    def __init__(self, grid: Grid, ground, cost, keep=None, c_b: float = 50.0):
+        import numpy as np
+        self.ground = np.ascontiguousarray(ground, dtype=np.float32)
+        self.cost = np.ascontiguousarray(cost, dtype=np.float32)
+        self.keep = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
+        if self.ground.shape != grid.shape or self.cost.shape != grid.shape:
+            raise ValueError(f"layers must be {grid.shape}")
+        if self.keep is not None and self.keep.shape != (grid.n_slices,):
+            raise ValueError("keep must have one flag per slice")
+        self.grid = grid
+        h = ctypes.c_void_p()
+        _check("tct_planner_create",
+               load().tct_planner_create(ctypes.byref(grid.c()), self.ground.ctypes.data,
+                                         self.cost.ctypes.data,
+                                         None if self.keep is None else self.keep.ctypes.data,
+                                         float(c_b), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tct_planner_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def plan(self, starts, goals, max_len: int = 4096, n_threads: int = 0):
+        """Plans every (start, goal) pair, each (i, j, slice).  Returns
+        (paths: list of int32 [len, 3] arrays, costs: float64 [n], expanded:
+        int64 [n]); an unreachable goal gives an empty path and cost inf."""
+        import numpy as np
+        st = np.ascontiguousarray(np.asarray(starts, dtype=np.int32).reshape(-1, 3))
+        go = np.ascontiguousarray(np.asarray(goals, dtype=np.int32).reshape(-1, 3))
+        if st.shape != go.shape:
+            raise ValueError("starts and goals differ in count")
+        n = len(st)
+        out = np.zeros((n, max_len, 3), np.int32)
+        lens = np.zeros(n, np.int32)
+        costs = np.zeros(n, np.float64)
+        expanded = np.zeros(n, np.int64)
+        _check("tct_plan_paths",
+               load().tct_plan_paths(self._h, n, st.ctypes.data, go.ctypes.data, max_len,
+                                     out.ctypes.data, lens.ctypes.data, costs.ctypes.data,
+                                     expanded.ctypes.data, n_threads))
+        return [out[q, :lens[q]].copy() for q in range(n)], costs, expanded
