@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-map batched-versus-plain measurement")
+    ap.add_argument("--no-planner", action="store_true",
+                    help="skip the path search across slices and the refinement of its paths")
     ap.add_argument("--no-stress", action="store_true",
                     help="skip the 60M-point cave-terrain measurement")
     return ap.parse_args()
@@ -273,6 +275,74 @@ def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps, paths=256
         out.update({"refine_%d_steps_ms" % refine_steps: t_ref,
                     "waypoint_steps_per_s": refine_steps * q / (t_ref * 1e-3),
                     "mean_cost_before": before, "mean_cost_after": float(c_out.mean())})
+    return out
+
+
+def planned_paths(dev, grid, params, ground, cost, keep, stats, n_paths=256, L=512, steps=50):
+    """Path search across the kept slices (the library's host stage) between
+    random traversable cells of the kept slices, on the host cores; the
+    found paths, resampled to L waypoints by arc length, are then refined by
+    the fused descent kernel."""
+    import numpy as np
+    import torch
+    from paper_2403_07631_gb300 import tct
+    st = tct.stats_from(stats)
+    g = tct.Grid(grid.x0, grid.y0, grid.res, grid.W, grid.H, grid.d_s, grid.n_slices,
+                 float(st.z_min), True)
+    t0 = time.perf_counter()
+    h_ground, h_cost, h_keep = ground.cpu().numpy(), cost.cpu().numpy(), keep.cpu().numpy()
+    t_copy = time.perf_counter() - t0
+    c_b = float(np.float32(params["c_b"]))
+    rng = np.random.default_rng(4)
+    kept = np.flatnonzero(h_keep)
+    trav = [np.flatnonzero(h_cost[k].reshape(-1) < c_b) for k in kept]
+    weights = np.array([len(t) for t in trav], np.float64)
+    ends = []
+    for _ in range(2 * n_paths):
+        m = rng.choice(len(kept), p=weights / weights.sum())
+        c = int(rng.choice(trav[m]))
+        ends.append((c // grid.W, c % grid.W, int(kept[m])))
+    starts, goals = ends[:n_paths], ends[n_paths:]
+    planner = tct.Planner(g, h_ground, h_cost, h_keep, c_b)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    paths, costs, expanded = planner.plan(starts, goals, max_len=1 << 16, n_threads=threads)
+    t_plan = time.perf_counter() - t0
+    planner.close()
+    reached = [p for p in paths if len(p) >= 2]
+    out = {"workload": "%d start/goal pairs on traversable cells of the kept slices" % n_paths,
+           "threads": threads, "plan_s": t_plan, "copy_to_host_s": t_copy,
+           "paths_per_s": n_paths / t_plan, "reached": len(reached),
+           "mean_states_expanded": float(np.mean(expanded)),
+           "mean_path_states": float(np.mean([len(p) for p in reached])) if reached else 0.0,
+           "paths_crossing_slices": sum(int(len(set(p[:, 2].tolist())) > 1) for p in reached)}
+    if not reached:
+        return out
+    # arc-length resampling of the cell-centre polylines
+    xy = np.empty((len(reached), L, 2), np.float32)
+    sl = np.empty((len(reached), L), np.int32)
+    for r, p in enumerate(reached):
+        pts = np.stack([grid.x0 + (p[:, 1] + 0.5) * grid.res,
+                        grid.y0 + (p[:, 0] + 0.5) * grid.res], 1)
+        s = np.concatenate([[0.0], np.cumsum(np.hypot(*np.diff(pts, axis=0).T))])
+        u = np.linspace(0.0, s[-1], L)
+        xy[r, :, 0] = np.interp(u, s, pts[:, 0])
+        xy[r, :, 1] = np.interp(u, s, pts[:, 1])
+        sl[r] = p[np.minimum(np.searchsorted(s, u, side="right") - 1, len(p) - 1), 2]
+    d_xy = torch.from_numpy(xy).to(dev)
+    d_sl = torch.from_numpy(sl).to(dev)
+    c_out = torch.empty(d_sl.shape, device=dev)
+    tct.tct_sample_cost(g, cost, None, d_xy, d_sl, c_out, None)
+    before = float(c_out.mean())
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    a.record(stream)
+    tct.tct_refine_paths(g, cost, d_sl, d_xy, steps, 1e-3, 1.0)
+    b.record(stream)
+    b.synchronize()
+    tct.tct_sample_cost(g, cost, None, d_xy, d_sl, c_out, None)
+    out.update({"refine_%d_steps_ms" % steps: a.elapsed_time(b),
+                "mean_cost_before": before, "mean_cost_after": float(c_out.mean())})
     return out
 
 
@@ -534,6 +604,8 @@ def main():
         "kept_slices": int(st.n_kept),
     }
     out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
+    if not args.no_planner:
+        out["planned_paths"] = planned_paths(dev, grid, params, ground, cost, keep, stats)
     if not args.no_batched:
         del ws, ground, ceil, cost, mask, keep
         torch.cuda.empty_cache()

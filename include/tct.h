@@ -6,11 +6,13 @@
  *   Sec. III-A / Alg. 1 (construction)  tomogram construction (tct_build)
  *   Sec. III-B / Eq. 1-6            scene evaluation (tct_evaluate)
  *   Sec. III-C / Eq. 7-9            slice simplification (tct_evaluate)
+ *   Sec. III-D                      path search across slices (tct_planner_*, host)
  *   Sec. III-E / Eq. 10             cost and elevation queries (tct_sample_cost)
  *
  * Conventions shared by every entry point:
  *   - Pointers named d_* are device pointers; h_* are host pointers.  The
- *     caller owns every buffer; the library never allocates memory.
+ *     caller owns every buffer; the library never allocates device memory
+ *     (the host-side planner keeps its own host tables).
  *   - Calls are asynchronous on `stream` (NULL = the legacy default stream)
  *     and perform no host synchronisation, so a sequence of calls can be
  *     captured into a CUDA graph.
@@ -307,9 +309,11 @@ int tct_build_evaluate_noalloc(const float *d_xyz, int64_t n, int32_t stride,
 /*
  * A planner over an evaluated tomogram in HOST memory: h_ground and h_cost
  * are the [N][H][W] e^G and c^T layers (grid->n_slices = N), h_keep the keep
- * flags (NULL: every slice).  The planner reads the caller's arrays in place
- * (no copy): they must stay alive and unchanged until tct_planner_destroy.
- * Only grid->H, W, n_slices and res are used; c_b is the barrier cost c^B.
+ * flags (NULL: every slice).  The planner copies what it reads into a table
+ * of 12 bytes per (kept slice, cell): ground, c^T and node cost; the
+ * caller's arrays are not used after this call.  Only grid->H, W, n_slices
+ * and res are used; c_b is the barrier cost c^B.  TCT_ERR_UNSUPPORTED when
+ * the table cannot be allocated.
  *
  * The graph is that of Sec. III-D on the kept slices: a state is a cell on
  * one kept slice and connects to its 8 neighbours on that slice; cells of

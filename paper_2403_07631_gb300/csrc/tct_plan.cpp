@@ -41,26 +41,31 @@ constexpr uint8_t kFromAbove = 9;   // reached through a gateway from slice m+1
 constexpr int kDi[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
 constexpr int kDj[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
 
+// Per-state search record, one cache-friendly 16 bytes: the best cost so
+// far, the query it belongs to (records of earlier queries read as unseen)
+// and the move that reached it.
+struct Record {
+    double g;
+    uint32_t epoch;
+    uint8_t from;
+};
+
 struct Search {
-    std::vector<double> g;
-    std::vector<uint32_t> epoch;
-    std::vector<uint8_t> from;
+    std::vector<Record> rec;
     uint32_t current = 0;
 
     void prepare(size_t states)
     {
-        if (g.size() != states) {
-            g.assign(states, 0.0);
-            epoch.assign(states, 0u);
-            from.assign(states, kFromStart);
+        if (rec.size() != states) {
+            rec.assign(states, Record{0.0, 0u, kFromStart});
             current = 0;
         }
         if (++current == 0) {   // wrapped: forget every earlier query
-            std::fill(epoch.begin(), epoch.end(), 0u);
+            for (auto &r : rec) r.epoch = 0u;
             current = 1;
         }
     }
-    bool seen(size_t s) const { return epoch[s] == current; }
+    bool seen(size_t s) const { return rec[s].epoch == current; }
 };
 
 struct Entry {
@@ -76,31 +81,50 @@ struct Entry {
 
 }  // namespace
 
+// What the search reads of one (kept slice, cell) state, packed together:
+// its ground elevation, its c^T and the c^N of its node (c^B where the
+// ground is invalid).
+struct StateInfo {
+    float e, t, cn;
+};
+
 struct tct_planner {
     int32_t H = 0, W = 0;
     float res = 0.f;
     float c_b = 0.f;
-    const float *ground = nullptr;   // [N][H][W], caller-owned
-    const float *cost = nullptr;     // [N][H][W], caller-owned
     std::vector<int32_t> kept;       // original index of kept slice m
+    std::vector<StateInfo> info;     // [M][H][W]
     std::mutex mu;
     std::vector<std::unique_ptr<Search>> idle;
 
     int64_t HW() const { return (int64_t)H * W; }
     int32_t M() const { return (int32_t)kept.size(); }
-    float G(int32_t m, int64_t cell) const { return ground[(int64_t)kept[m] * HW() + cell]; }
-    float T(int32_t m, int64_t cell) const { return cost[(int64_t)kept[m] * HW() + cell]; }
+    const StateInfo &at(int32_t m, int64_t cell) const { return info[(size_t)(m * HW() + cell)]; }
 
-    // c^N of the node (m, cell): minimum c^T over the run of kept slices
-    // around m with the same ground elevation; c^B for a cell without ground
-    double node_cost(int32_t m, int64_t cell) const
+    // the table, from the caller's [N][H][W] layers: c^N of (m, cell) is the
+    // minimum c^T over the run of kept slices around m with the same ground
+    void fill(const float *ground, const float *cost)
     {
-        const float e = G(m, cell);
-        if (!std::isfinite(e)) return c_b;
-        float c = T(m, cell);
-        for (int32_t a = m - 1; a >= 0 && G(a, cell) == e; --a) c = std::min(c, T(a, cell));
-        for (int32_t b = m + 1; b < M() && G(b, cell) == e; ++b) c = std::min(c, T(b, cell));
-        return c;
+        const int64_t hw = HW();
+        const int32_t nm = M();
+        info.resize((size_t)nm * hw);
+        for (int64_t c = 0; c < hw; ++c) {
+            for (int32_t m = 0; m < nm;) {
+                const float e = ground[(int64_t)kept[m] * hw + c];
+                int32_t b = m + 1;
+                float lo = cost[(int64_t)kept[m] * hw + c];
+                if (std::isfinite(e))
+                    for (; b < nm && ground[(int64_t)kept[b] * hw + c] == e; ++b)
+                        lo = std::min(lo, cost[(int64_t)kept[b] * hw + c]);
+                for (int32_t a = m; a < b; ++a) {
+                    StateInfo &si = info[(size_t)(a * hw + c)];
+                    si.e = e;
+                    si.t = cost[(int64_t)kept[a] * hw + c];
+                    si.cn = std::isfinite(e) ? lo : c_b;
+                }
+                m = b;
+            }
+        }
     }
 
     std::unique_ptr<Search> take()
@@ -153,8 +177,8 @@ void run_query(const tct_planner &p, Search &S, const Query &q, Result &r)
     const int32_t ms = kept_index(p, q.start[2]), mg = kept_index(p, q.goal[2]);
     const int64_t cs = (int64_t)q.start[0] * p.W + q.start[1];
     const int64_t cg = (int64_t)q.goal[0] * p.W + q.goal[1];
-    const float eg = p.G(mg, cg);
-    if (!(p.node_cost(ms, cs) < p.c_b) || !(p.node_cost(mg, cg) < p.c_b)) return;
+    const float eg = p.at(mg, cg).e;
+    if (!(p.at(ms, cs).cn < p.c_b) || !(p.at(mg, cg).cn < p.c_b)) return;
 
     const int gi = q.goal[0], gj = q.goal[1];
     auto h = [&](int i, int j) {
@@ -163,18 +187,15 @@ void run_query(const tct_planner &p, Search &S, const Query &q, Result &r)
     };
     std::priority_queue<Entry> open;
     const int64_t s0 = (int64_t)ms * HW + cs;
-    S.epoch[s0] = S.current;
-    S.g[s0] = 0.0;
-    S.from[s0] = kFromStart;
+    S.rec[s0] = Record{0.0, S.current, kFromStart};
     open.push({h(q.start[0], q.start[1]), 0.0, s0});
     const double res = (double)p.res;
     int64_t reached = -1;
 
     auto relax = [&](int64_t t, double g, uint8_t code, int ti, int tj) {
-        if (!S.seen(t) || g < S.g[t]) {
-            S.epoch[t] = S.current;
-            S.g[t] = g;
-            S.from[t] = code;
+        Record &rt = S.rec[t];
+        if (rt.epoch != S.current || g < rt.g) {
+            rt = Record{g, S.current, code};
             open.push({g + h(ti, tj), g, t});
         }
     };
@@ -182,12 +203,13 @@ void run_query(const tct_planner &p, Search &S, const Query &q, Result &r)
     while (!open.empty()) {
         const Entry top = open.top();
         open.pop();
-        if (top.g > S.g[top.s]) continue;   // stale entry
+        if (top.g > S.rec[top.s].g) continue;   // stale entry
         ++r.expanded;
         const int32_t m = (int32_t)(top.s / HW);
         const int64_t c = top.s % HW;
         const int i = (int)(c / p.W), j = (int)(c % p.W);
-        const float e = p.G(m, c);
+        const StateInfo &here = p.at(m, c);
+        const float e = here.e;
         if (c == cg && e == eg) {
             reached = top.s;
             break;
@@ -196,30 +218,30 @@ void run_query(const tct_planner &p, Search &S, const Query &q, Result &r)
             const int ni = i + kDi[d], nj = j + kDj[d];
             if (ni < 0 || ni >= p.H || nj < 0 || nj >= p.W) continue;
             const int64_t nc = (int64_t)ni * p.W + nj;
-            const float ne = p.G(m, nc);
-            if (!std::isfinite(ne)) continue;
-            const double cn = p.node_cost(m, nc);
+            const StateInfo &there = p.at(m, nc);
+            const double cn = there.cn;   // c^B where the ground is invalid
             if (!(cn < p.c_b)) continue;
+            const float ne = there.e;
             const double dz = ((double)ne - (double)e) / res;
             const double planar = (kDi[d] != 0 && kDj[d] != 0) ? 2.0 : 1.0;
             relax((int64_t)m * HW + nc, top.g + (cn + std::sqrt(planar + dz * dz)), (uint8_t)d,
                   ni, nj);
         }
         // gateways: the same node on the adjacent kept slice, cheaper there
-        if (m + 1 < M && p.G(m + 1, c) == e && p.T(m + 1, c) < p.T(m, c))
+        if (m + 1 < M && p.at(m + 1, c).e == e && p.at(m + 1, c).t < here.t)
             relax((int64_t)(m + 1) * HW + c, top.g, kFromBelow, i, j);
-        if (m > 0 && p.G(m - 1, c) == e && p.T(m - 1, c) < p.T(m, c))
+        if (m > 0 && p.at(m - 1, c).e == e && p.at(m - 1, c).t < here.t)
             relax((int64_t)(m - 1) * HW + c, top.g, kFromAbove, i, j);
     }
     if (reached < 0) return;
-    r.cost = S.g[reached];
+    r.cost = S.rec[reached].g;
     for (int64_t s = reached;;) {
         const int32_t m = (int32_t)(s / HW);
         const int64_t c = s % HW;
         r.path.push_back((int32_t)(c / p.W));
         r.path.push_back((int32_t)(c % p.W));
         r.path.push_back(p.kept[m]);
-        const uint8_t f = S.from[s];
+        const uint8_t f = S.rec[s].from;
         if (f == kFromStart) break;
         if (f == kFromBelow) s -= HW;
         else if (f == kFromAbove) s += HW;
@@ -251,14 +273,13 @@ int tct_planner_create(const tct_grid *grid, const float *h_ground, const float 
         p->W = grid->W;
         p->res = grid->res;
         p->c_b = c_b;
-        p->ground = h_ground;
-        p->cost = h_cost;
         for (int32_t k = 0; k < grid->n_slices; ++k)
             if (!h_keep || h_keep[k]) p->kept.push_back(k);
-    } catch (...) {
-        return TCT_ERR_INVALID_ARG;
+        if (p->kept.empty()) return TCT_ERR_INVALID_ARG;
+        p->fill(h_ground, h_cost);
+    } catch (...) {   // the state table could not be allocated
+        return TCT_ERR_UNSUPPORTED;
     }
-    if (p->kept.empty()) return TCT_ERR_INVALID_ARG;
     *out = p.release();
     return TCT_OK;
 }

@@ -469,8 +469,8 @@ def tct_launch_count() -> int:
 class Planner:
     """Path search across the kept slices (tct_planner_*, a host stage of the
     library): ground / cost are host numpy [N, H, W] float32 layers, keep
-    the [N] keep flags (None: all slices).  The arrays are held for the
-    planner's lifetime; the library reads them in place."""
+    the [N] keep flags (None: all slices).  The library copies what it needs
+    (12 bytes per kept slice and cell) when the planner is made."""
 
     def __init__(self, grid: Grid, ground, cost, keep=None, c_b: float = 50.0):
         import numpy as np
