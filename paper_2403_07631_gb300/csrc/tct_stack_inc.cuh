@@ -19,6 +19,7 @@
 // while the writes of every slice's layers (the algorithmic bytes) are
 // always done.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -47,14 +48,18 @@ struct Geo {
     static constexpr int CWW = (CW + 31) / 32 + 1;                // c^init change words (+pad)
     static constexpr int GPASS = (GW + 31) / 32, CPASS = (CW + 31) / 32;
     static constexpr int WORDS = 4 * EH * EWW + 2 * GH * GWW + CH * CWW;
+    static_assert(NE < 65536, "16-bit indices of the elevation region");
     static constexpr size_t smem_bytes() {
+        // state, change words, 16-bit pointer offsets, 16-bit list of the
+        // cells a plane passed
         return sizeof(float) * (2 * NE + CW * CH) + sizeof(uint32_t) * WORDS +
-               ((sizeof(uint16_t) * NE + 15) / 16) * 16;
+               2 * (((sizeof(uint16_t) * NE + 15) / 16) * 16);
     }
 };
 
 // Shared state of the per-slice counters, kept in static shared memory.
 struct SliceCounters {
+    int32_t nlist[2];                  // cells a plane passed, slices of even / odd k
     int32_t upre[TCT_MAX_SLICES + 1];
     int32_t valid[TCT_MAX_SLICES + 1];
     int32_t trav[TCT_MAX_SLICES + 1];
@@ -111,12 +116,14 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     uint32_t *sGChg = sGB + G::GH * G::GWW;
     uint32_t *sCIChg = sGChg + G::GH * G::GWW;
     uint16_t *sOff = reinterpret_cast<uint16_t *>(sCIChg + G::CH * G::CWW);
+    uint16_t *sList = sOff + ((sizeof(uint16_t) * G::NE + 15) / 16) * 8;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t HW = (int64_t)a.W * a.H;
     const float ts2 = c.theta_s * c.theta_s;   // m^grad < theta_s  <=>  m^2 < theta_s^2
     const float inv_ts2 = c.inv_ts * c.inv_ts;
 
+    if (tid < 2) counters.nlist[tid] = 0;
     for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
         s_upre[i] = 0;
         s_valid[i] = 0;
@@ -156,9 +163,71 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     auto run_get = [&](int q) -> int {
         return q < 4 ? (run_lo >> (8 * q)) & 0xffu : (run_hi >> (8 * (q - 4))) & 0xffu;
     };
+    // per cell, an upper bound of c^T over its run before the current slice:
+    // fp16 rounded up (never below the true maximum), -inf for an empty run;
+    // a cell whose cost is not below it cannot set a bit of U(p, k-1) for p
+    // in the run, so its walk is skipped
+    uint32_t rmax[kStrip / 2];
+#pragma unroll
+    for (int q = 0; q < kStrip / 2; ++q) rmax[q] = 0xfc00fc00u;
+    auto rmax_get = [&](int q) -> float {
+        const unsigned short hb = (unsigned short)(rmax[q >> 1] >> (16 * (q & 1)));
+        return __half2float(__ushort_as_half(hb));
+    };
+    auto rmax_set = [&](int q, unsigned short hb) {
+        const int sh = 16 * (q & 1);
+        rmax[q >> 1] = (rmax[q >> 1] & ~(0xffffu << sh)) | ((uint32_t)hb << sh);
+    };
     auto run_set = [&](int q, int v) {
         if (q < 4) run_lo = (run_lo & ~(0xffu << (8 * q))) | ((uint32_t)v << (8 * q));
         else run_hi = (run_hi & ~(0xffu << (8 * (q - 4)))) | ((uint32_t)v << (8 * (q - 4)));
+    };
+    // U(p, kk) |= [c^T_kk < c^T_p] for p in the equal-ground run [r0, kk) of
+    // each cell of the strip in `walk` (cT holds slice kk).  The earlier
+    // slices' costs are read back from the output, four slices at a time, so
+    // that the loads of a cell overlap; the bits gather in
+    // registers and leave with one atomic per word and warp.  Called by the
+    // whole warp.
+    auto mark_run = [&](uint32_t walk, int kk) {
+        uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+        int lo = kk;
+#pragma unroll
+        for (int q = 0; q < kStrip; ++q)
+            if ((walk >> q) & 1u) lo = min(lo, run_get(q));
+        const int64_t cell0 = (int64_t)(ty0 + tr0) * a.W + j_out;
+        for (int p = lo; p < kk; p += 4) {
+#pragma unroll
+            for (int q = 0; q < kStrip; ++q) {
+                if (!((walk >> q) & 1u)) continue;
+                const int r0 = run_get(q);
+                const int64_t cell = cell0 + (int64_t)q * a.W;
+                float cp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    cp[u] = (p + u >= r0 && p + u < kk) ? a.cost[(int64_t)(p + u) * HW + cell]
+                                                        : -INFINITY;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int bit = p + u + 1, w = bit >> 5;
+                    const uint32_t m = cT[q] < cp[u] ? 1u << (bit & 31) : 0u;
+                    u0 |= w == 0 ? m : 0u;
+                    u1 |= w == 1 ? m : 0u;
+                    u2 |= w == 2 ? m : 0u;
+                    u3 |= w == 3 ? m : 0u;
+                }
+            }
+        }
+        u0 = __reduce_or_sync(0xffffffffu, u0);
+        u1 = __reduce_or_sync(0xffffffffu, u1);
+        u2 = __reduce_or_sync(0xffffffffu, u2);
+        u3 = __reduce_or_sync(0xffffffffu, u3);
+        if (lane == 0) {
+            uint32_t *ub = a.ubits + 4 * kk;
+            if (u0) atomicOr(ub + 0, u0);
+            if (u1) atomicOr(ub + 1, u1);
+            if (u2) atomicOr(ub + 2, u2);
+            if (u3) atomicOr(ub + 3, u3);
+        }
     };
     __syncthreads();
 
@@ -169,28 +238,52 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         uint32_t *sChgC = sChgC0 + (k & 1) * G::EH * G::EWW;
 
         // ---- 1. grounds and ceilings: advance the pointers past h ----
-        for (int e = tid; e < G::NE; e += kNT) {
-            float zc = sZC[e];
-            if (zc <= h) {
-                const int r = e / G::EW, s = e - r * G::EW;
-                const int64_t cell = (int64_t)(ty0 - G::HE + r) * a.W + (tx0 - G::HE + s);
-                const int32_t b = a.start[cell], end = a.start[cell + 1];
-                const float zg0 = sEG[e];
-                const uint32_t off = sOff[e];
-                int32_t p = off < kSat ? b + (int32_t)off : upper_bound(a.zs, b, end, zg0);
-                float zg;
-                do {
-                    zg = zc;
-                    ++p;
-                    zc = p < end ? a.zs[p] : INFINITY;
-                } while (zc <= h);
-                sEG[e] = zg;
-                sZC[e] = zc;
-                sOff[e] = (uint16_t)min((uint32_t)(p - b), kSat);
-                const uint32_t bit = 1u << (s & 31);
-                if (zg != zg0) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
-                atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
+        // 1a. list the cells whose next height the plane passed (one shared
+        //     counter add per warp)
+        int32_t *nlist = &counters.nlist[k & 1];
+        for (int base = 0; base < G::NE; base += kNT) {
+            const int e = base + tid;
+            const bool pass = e < G::NE && sZC[e] <= h;
+            const uint32_t m = __ballot_sync(0xffffffffu, pass);
+            if (m) {
+                int at = 0;
+                if (lane == 0) at = atomicAdd(nlist, __popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (pass) sList[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
             }
+        }
+        __syncthreads();
+        // 1b. advance the listed cells, spread evenly over the threads; each
+        //     round reads the next four heights of the segment at once, so a
+        //     cell that passes n heights waits for ceil(n / 4) loads, not n
+        const int n_pass = *nlist;
+        for (int t = tid; t < n_pass; t += kNT) {
+            const int e = sList[t];
+            const int r = e / G::EW, s = e - r * G::EW;
+            const int64_t cell = (int64_t)(ty0 - G::HE + r) * a.W + (tx0 - G::HE + s);
+            const int32_t b = a.start[cell], end = a.start[cell + 1];
+            const float zg0 = sEG[e];
+            const uint32_t off = sOff[e];
+            int32_t p = off < kSat ? b + (int32_t)off : upper_bound(a.zs, b, end, zg0);
+            float zg = sZC[e], zc;     // zs[p] <= h: the ground is at least that
+            for (;;) {
+                const float z1 = p + 1 < end ? a.zs[p + 1] : INFINITY;
+                const float z2 = p + 2 < end ? a.zs[p + 2] : INFINITY;
+                const float z3 = p + 3 < end ? a.zs[p + 3] : INFINITY;
+                const float z4 = p + 4 < end ? a.zs[p + 4] : INFINITY;
+                if (z1 > h) { zc = z1; p += 1; break; }
+                if (z2 > h) { zg = z1; zc = z2; p += 2; break; }
+                if (z3 > h) { zg = z2; zc = z3; p += 3; break; }
+                if (z4 > h) { zg = z3; zc = z4; p += 4; break; }
+                zg = z4;
+                p += 4;
+            }
+            sEG[e] = zg;
+            sZC[e] = zc;
+            sOff[e] = (uint16_t)min((uint32_t)(p - b), kSat);
+            const uint32_t bit = 1u << (s & 31);
+            if (zg != zg0) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
+            atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
         }
         __syncthreads();
 
@@ -199,6 +292,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             uint32_t *nG = sChgG0 + ((k + 1) & 1) * G::EH * G::EWW;
             uint32_t *nC = sChgC0 + ((k + 1) & 1) * G::EH * G::EWW;
             for (int i = tid; i < G::EH * G::EWW; i += kNT) { nG[i] = 0; nC[i] = 0; }
+            if (tid == 0) counters.nlist[(k + 1) & 1] = 0;
         }
 
         // ---- 2. gentle flags (Eq. 2: m^grad < theta_s) ----
@@ -365,20 +459,26 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             }
             // Eq. 9 of slice k-1 against slice k, then the rows p it is unique against
             int pre = 0;
+            uint32_t walk = 0;
 #pragma unroll
             for (int q = 0; q < kStrip; ++q) {
                 const int i = ty0 + tr0 + q;
                 const bool gq = (gchbits >> q) & 1u;
                 if (!first && i < a.H && j_out < a.W && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
-                    const int kk = k - 1, r0 = run_get(q);
-                    const int64_t cell = (int64_t)i * a.W + j_out;
-                    for (int p = r0; p < kk; ++p) {
-                        const float cp = a.cost[(int64_t)p * HW + cell];
-                        if (cT[q] < cp) atomicOr(&a.ubits[4 * kk + ((p + 1) >> 5)], 1u << ((p + 1) & 31));
-                    }
-                    pre = max(pre, r0 + 1);
+                    if (cT[q] < rmax_get(q)) walk |= 1u << q;
+                    pre = max(pre, run_get(q) + 1);
                 }
-                if (gq) run_set(q, k);
+            }
+            if (!first) mark_run(walk, k - 1);
+#pragma unroll
+            for (int q = 0; q < kStrip; ++q) {
+                if ((gchbits >> q) & 1u) {
+                    run_set(q, k);
+                    rmax_set(q, 0xfc00u);
+                } else if (!first) {
+                    const __half hc = __float2half_ru(cT[q]);
+                    if (__half2float(hc) > rmax_get(q)) rmax_set(q, __half_as_ushort(hc));
+                }
                 cT[q] = acc[q];
             }
             const int wmax = __reduce_max_sync(0xffffffffu, pre);
@@ -417,19 +517,16 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     // Eq. 9 holds vacuously for the last slice
     {
         int pre = 0;
+        uint32_t walk = 0;
 #pragma unroll
         for (int q = 0; q < kStrip; ++q) {
             const int i = ty0 + tr0 + q;
             if (i < a.H && j_out < a.W && cT[q] < c.c_b) {
-                const int kk = a.N - 1, r0 = run_get(q);
-                const int64_t cell = (int64_t)i * a.W + j_out;
-                for (int p = r0; p < kk; ++p) {
-                    const float cp = a.cost[(int64_t)p * HW + cell];
-                    if (cT[q] < cp) atomicOr(&a.ubits[4 * kk + ((p + 1) >> 5)], 1u << ((p + 1) & 31));
-                }
-                pre = max(pre, r0 + 1);
+                if (cT[q] < rmax_get(q)) walk |= 1u << q;
+                pre = max(pre, run_get(q) + 1);
             }
         }
+        mark_run(walk, a.N - 1);
         const int wmax = __reduce_max_sync(0xffffffffu, pre);
         if (lane == 0 && wmax > 0) atomicMax(&s_upre[a.N - 1], wmax);
     }
@@ -450,7 +547,10 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
 template <int RK, int RP, int TW, int TH>
 struct Occupancy {
     using G = Geo<RK, RP, TW, TH>;
-    static constexpr int by_smem = (int)(200000 / (G::smem_bytes() + 2048));
+    // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA,
+    // plus the CTA's static shared memory
+    static constexpr int by_smem =
+        (int)(233472 / (G::smem_bytes() + sizeof(SliceCounters) + 64 + 1024));
     static constexpr int by_regs = 65536 / (64 * G::NT);
     static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
 };
