@@ -150,7 +150,7 @@ def stack_traffic():
     """DRAM bytes per launch of the stack kernel from the committed ncu summary,
     or None when the kernel source changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_stack_inc_parking.txt")
+    path = os.path.join(ROOT, "profiles", "k_stack_batched_parking.txt")
     src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cuh")
     try:
         rec = {}
@@ -592,7 +592,7 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
                           "peak_source": peak_src},
-        "roofline": {"kernel": "k_stack_inc (per-tile incremental slice stack)", "bound": "hbm",
+        "roofline": {"kernel": "k_stack_batched<5,2,64,64> (per-tile incremental slice stack)", "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
                      "traffic": traffic, "algorithmic_bytes": sb, "ms": stack_ms,
                      "peak_source": peak_src},
