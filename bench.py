@@ -406,7 +406,7 @@ def batched_vs_plain(dev, params, steps):
             "batched_mpoints_per_s": P / (t_graph * 1e-3) / 1e6,
             "batched_slice_cells_per_s": SC / (t_graph * 1e-3),
             "path_roofline_frac": (12 * P + 13 * SC) / (t_graph * 1e-3) / 1e9 / measured_peak_gbs()[0],
-            "tuning": {"tile": {1: "64x64", 2: "32x32"}.get(tuning.tile, "auto"),
+            "tuning": {"tile": {1: "64x64", 2: "32x32", 3: "64x56"}.get(tuning.tile, "auto"),
                        "ctas_per_sm": tuning.ctas_per_sm,
                        "points_per_block": tuning.points_per_block}}
 

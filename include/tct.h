@@ -59,9 +59,10 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 #define TCT_MAX_BATCH 64               /* maps per batched call              */
 
 /* tile shapes of the slice-stack kernel (tct_tuning.tile) */
-#define TCT_TILE_AUTO 0                /* 64 x 64 unless that leaves SMs idle */
+#define TCT_TILE_AUTO 0                /* the shape with the least work per SM over whole waves */
 #define TCT_TILE_64 1                  /* 64 x 64 cells, 512 threads          */
 #define TCT_TILE_32 2                  /* 32 x 32 cells, 128 threads          */
+#define TCT_TILE_64x56 3               /* 64 x 56 cells, 448 threads          */
 
 /* ---- geometry (Sec. III-A) ---------------------------------------------- */
 #define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (first step of Alg. 1) */

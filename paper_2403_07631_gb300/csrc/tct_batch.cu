@@ -207,15 +207,7 @@ int run_batch(const tct_map *maps, int n_maps, const tct_params *params, const t
     if (e == cudaSuccess)
         e = launch_partition_batched(pin.data(), n_maps, tn.points_per_block, L.cells, ws, s);
     int tile = tn.tile;
-    if (tile == TCT_TILE_AUTO) {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int64_t tiles64 = 0;
-        for (int i = 0; i < n_maps; ++i)
-            tiles64 += (int64_t)((sargs[i].W + 63) / 64) * ((sargs[i].H + 63) / 64);
-        tile = tiles64 < 2 * sms ? TCT_TILE_32 : TCT_TILE_64;
-    }
+    if (tile == TCT_TILE_AUTO) tile = choose_tile(c, n_maps, sorted.data(), 2);
     if (e == cudaSuccess)
         e = launch_stack_batched(c, n_maps, sorted.data(), queue, tile, tn.ctas_per_sm, s);
     if (e == cudaSuccess) {
@@ -260,7 +252,8 @@ extern "C" int tct_build_evaluate_batched(const tct_map *h_maps, int32_t n_maps,
     if (ws_bytes < batch_layout(h_maps, n_maps).total) return TCT_ERR_WORKSPACE_TOO_SMALL;
     tct_tuning tn = tuning ? *tuning : default_tuning();
     if (tn.points_per_block < 4 || tn.points_per_block % 4) return TCT_ERR_INVALID_ARG;
-    if (tn.tile != TCT_TILE_AUTO && tn.tile != TCT_TILE_64 && tn.tile != TCT_TILE_32)
+    if (tn.tile != TCT_TILE_AUTO && tn.tile != TCT_TILE_64 && tn.tile != TCT_TILE_32 &&
+        tn.tile != TCT_TILE_64x56)
         return TCT_ERR_INVALID_ARG;
     return run_batch(h_maps, n_maps, params, tn, c, d_ws, (cudaStream_t)stream);
 }
@@ -277,7 +270,7 @@ extern "C" int tct_autotune_batched(const tct_map *h_maps, int32_t n_maps,
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return TCT_ERR_CUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return TCT_ERR_CUDA; }
-    const int tiles[] = {TCT_TILE_64, TCT_TILE_32};
+    const int tiles[] = {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_32};
     const int ctas[] = {0, 1};
     const int ppb[] = {2048, 8192};
     float best = INFINITY;

@@ -120,6 +120,10 @@ bool inc_supported(const EvalConsts &c, int n_slices);
 cudaError_t launch_stack_inc(const StackArgs &a, int32_t *queue, int tile, cudaStream_t s);
 // One persistent launch over the tiles of n_maps maps (largest first);
 // queue must be zero when the launch starts.
+// The automatic tile shape of the incremental stack: 32 x 32 when the 64 x 64
+// tiles of all maps number fewer than small_tiles64 per SM, otherwise the
+// shape with the least work per SM over whole waves of resident CTAs.
+int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t small_tiles64);
 cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,
                                  int32_t *queue, int tile, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits,

@@ -431,14 +431,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     k_stack_init<<<1, 128, 0, s>>>(upre, ubits, lists ? lists->queue : nullptr);
     count_launches(1);
     if (lists) {
-        if (tile == TCT_TILE_AUTO) {
-            // 64 x 64 tiles unless they leave SMs idle
-            int dev = 0, sms = 148;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int64_t tiles64 = (int64_t)((g.W + 63) / 64) * ((g.H + 63) / 64);
-            tile = tiles64 < sms ? TCT_TILE_32 : TCT_TILE_64;
-        }
+        if (tile == TCT_TILE_AUTO && inc_supported(c, a.N)) tile = choose_tile(c, 1, &a, 1);
         const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
         if (e != cudaErrorNotSupported) return e;
         return pick_tile<true, false>(a, s);

@@ -26,7 +26,55 @@ cudaError_t dispatch(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t
     return cudaErrorNotSupported;
 }
 
+// Tile edge lengths of a TCT_TILE_* shape.
+void tile_dims(int tile, int *TW, int *TH) {
+    *TW = tile == TCT_TILE_32 ? 32 : 64;
+    *TH = tile == TCT_TILE_32 ? 32 : tile == TCT_TILE_64x56 ? 56 : 64;
+}
+
+// Resident CTAs per SM of an instance (the estimate its launch bounds use).
+template <int RK, int RP>
+int resident(int tile) {
+    if (tile == TCT_TILE_32) return inc::Occupancy<RK, RP, 32, 32>::value;
+    if (tile == TCT_TILE_64x56) return inc::Occupancy<RK, RP, 64, 56>::value;
+    return inc::Occupancy<RK, RP, 64, 64>::value;
+}
+
+int resident_for(const EvalConsts &c, int tile) {
+    if (c.rk == 5) return resident<5, 2>(tile);
+    if (c.rk == 4) return resident<4, 2>(tile);
+    return resident<12, 2>(tile);
+}
+
 }  // namespace
+
+int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t small_tiles64) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t tiles64 = 0;
+    for (int i = 0; i < n_maps; ++i)
+        tiles64 += (int64_t)((maps[i].W + 63) / 64) * ((maps[i].H + 63) / 64);
+    if (tiles64 < small_tiles64 * sms) return TCT_TILE_32;   // small maps: more, smaller CTAs
+    // whole waves of resident CTAs times the cells (with halo) a CTA handles
+    const int he = c.rk + c.patch_radius + 1;
+    int best = TCT_TILE_64;
+    double best_cost = INFINITY;
+    for (int tile : {TCT_TILE_64, TCT_TILE_64x56}) {
+        int TW, TH;
+        tile_dims(tile, &TW, &TH);
+        int64_t tiles = 0;
+        for (int i = 0; i < n_maps; ++i)
+            tiles += (int64_t)((maps[i].W + TW - 1) / TW) * ((maps[i].H + TH - 1) / TH);
+        const int64_t slots = (int64_t)sms * (resident_for(c, tile) > 0 ? resident_for(c, tile) : 1);
+        const double cost = (double)((tiles + slots - 1) / slots) * (TW + 2 * he) * (TH + 2 * he);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = tile;
+        }
+    }
+    return best;
+}
 
 bool inc_supported(const EvalConsts &c, int n_slices) {
     if (n_slices > 255) return false;                // run starts are kept in bytes
@@ -47,7 +95,8 @@ cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArg
     b.c = c;
     b.n_maps = n_maps;
     b.queue = queue;
-    const int TW = tile == TCT_TILE_32 ? 32 : 64, TH = TW;
+    int TW, TH;
+    tile_dims(tile, &TW, &TH);
     int total = 0;
     for (int i = 0; i < n_maps; ++i) {
         b.maps[i] = inc_map(maps[i]);

@@ -617,6 +617,7 @@ cudaError_t run_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
 template <int RK, int RP>
 cudaError_t run_radius(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t s) {
     if (tile == TCT_TILE_32) return run_batched<RK, RP, 32, 32>(b, ctas_per_sm, s);
+    if (tile == TCT_TILE_64x56) return run_batched<RK, RP, 64, 56>(b, ctas_per_sm, s);
     return run_batched<RK, RP, 64, 64>(b, ctas_per_sm, s);
 }
 
