@@ -60,6 +60,7 @@ struct Geo {
 // Shared state of the per-slice counters, kept in static shared memory.
 struct SliceCounters {
     int32_t nlist[2];                  // cells a plane passed, slices of even / odd k
+    int32_t nwork[2];                  // dirty row blocks: gentle flags, c^init
     int32_t upre[TCT_MAX_SLICES + 1];
     int32_t valid[TCT_MAX_SLICES + 1];
     int32_t trav[TCT_MAX_SLICES + 1];
@@ -241,6 +242,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         // 1a. list the cells whose next height the plane passed (one shared
         //     counter add per warp)
         int32_t *nlist = &counters.nlist[k & 1];
+        if (tid == 0) counters.nwork[0] = counters.nwork[1] = 0;   // read before the last barrier
         for (int base = 0; base < G::NE; base += kNT) {
             const int e = base + tid;
             const bool pass = e < G::NE && sZC[e] <= h;
@@ -296,17 +298,38 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         }
 
         // ---- 2. gentle flags (Eq. 2: m^grad < theta_s) ----
-#pragma unroll 1
-        for (int gr = warp; gr < G::GH; gr += kNW) {
-#pragma unroll
-            for (int w = 0; w < G::GPASS; ++w) {
-                // stencil rows gr..gr+2 of the elevation region, columns 32w..32w+33
+        // 2a. one lane per 32-column row block: the block is dirty when a
+        //     ground of its stencil rows (gr..gr+2, columns 32w..32w+33 of
+        //     the elevation region) changed; dirty blocks are listed, clean
+        //     ones get a zero change word
+        for (int base = 32 * warp; base < G::GH * G::GPASS; base += 32 * kNW) {
+            const int blk = base + lane;
+            bool dirty = false;
+            if (blk < G::GH * G::GPASS) {
+                const int gr = blk / G::GPASS, w = blk - gr * G::GPASS;
                 uint32_t v = 0;
-                if (lane < 6) v = sChgG[(gr + (lane >> 1)) * G::EWW + w + (lane & 1)];
-                if (!first && !__any_sync(0xffffffffu, v != 0)) {
-                    if (lane == 0) sGChg[gr * G::GWW + w] = 0;
-                    continue;
-                }
+#pragma unroll
+                for (int dr = 0; dr < 3; ++dr)
+                    v |= sChgG[(gr + dr) * G::EWW + w] | sChgG[(gr + dr) * G::EWW + w + 1];
+                dirty = first || v != 0;
+                if (!dirty) sGChg[gr * G::GWW + w] = 0;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, dirty);
+            if (m) {
+                int at = 0;
+                if (lane == 0) at = atomicAdd(&counters.nwork[0], __popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (dirty) sList[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)blk;
+            }
+        }
+        __syncthreads();
+        // 2b. the listed blocks, spread over all warps
+        {
+            const int n_blk = counters.nwork[0];
+#pragma unroll 1
+            for (int t = warp; t < n_blk; t += kNW) {
+                const int blk = sList[t];
+                const int gr = blk / G::GPASS, w = blk - gr * G::GPASS;
                 const int gs = 32 * w + lane;
                 const int gsc = gs < G::GW ? gs : G::GW - 1;
                 const float *ep = sEG + (gr + 1) * G::EW + (gsc + 1);
@@ -346,19 +369,40 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         }
 
         // ---- 3. interval (Eq. 1), terrain (Eq. 3-4), initial cost (Eq. 5) ----
-#pragma unroll 1
-        for (int cr = warp; cr < G::CH; cr += kNW) {
+        // 3a. one lane per 32-column row block of the c^init region: dirty when
+        //     a ground of rows cr+RP..cr+RP+2, the ceiling of row cr+RP+1 or a
+        //     gentle flag of rows cr..cr+2RP changed; listed as in step 2
+        for (int base = 32 * warp; base < G::CH * G::CPASS; base += 32 * kNW) {
+            const int blk = base + lane;
+            bool dirty = false;
+            if (blk < G::CH * G::CPASS) {
+                const int cr = blk / G::CPASS, w = blk - cr * G::CPASS;
+                uint32_t v = sChgC[(cr + RP + 1) * G::EWW + w] | sChgC[(cr + RP + 1) * G::EWW + w + 1];
 #pragma unroll
-            for (int w = 0; w < G::CPASS; ++w) {
-                uint32_t v = 0;
-                if (lane < 6) v = sChgG[(cr + RP + (lane >> 1)) * G::EWW + w + (lane & 1)];
-                else if (lane < 8) v = sChgC[(cr + RP + 1) * G::EWW + w + (lane & 1)];
-                else if (lane < 8 + 2 * (2 * RP + 1))
-                    v = sGChg[(cr + ((lane - 8) >> 1)) * G::GWW + w + (lane & 1)];
-                if (!first && !__any_sync(0xffffffffu, v != 0)) {
-                    if (lane == 0) sCIChg[cr * G::CWW + w] = 0;
-                    continue;
-                }
+                for (int dr = 0; dr < 3; ++dr)
+                    v |= sChgG[(cr + RP + dr) * G::EWW + w] | sChgG[(cr + RP + dr) * G::EWW + w + 1];
+#pragma unroll
+                for (int dr = 0; dr <= 2 * RP; ++dr)
+                    v |= sGChg[(cr + dr) * G::GWW + w] | sGChg[(cr + dr) * G::GWW + w + 1];
+                dirty = first || v != 0;
+                if (!dirty) sCIChg[cr * G::CWW + w] = 0;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, dirty);
+            if (m) {
+                int at = 0;
+                if (lane == 0) at = atomicAdd(&counters.nwork[1], __popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (dirty) sList[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)blk;
+            }
+        }
+        __syncthreads();
+        // 3b. the listed blocks, spread over all warps
+        {
+            const int n_blk = counters.nwork[1];
+#pragma unroll 1
+            for (int t = warp; t < n_blk; t += kNW) {
+                const int blk = sList[t];
+                const int cr = blk / G::CPASS, w = blk - cr * G::CPASS;
                 const int cs = 32 * w + lane;
                 bool changed = false;
                 if (cs < G::CW) {
