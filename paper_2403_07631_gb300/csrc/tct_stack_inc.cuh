@@ -166,11 +166,14 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     };
     // per cell, an upper bound of c^T over its run before the current slice:
     // fp16 rounded up (never below the true maximum), -inf for an empty run;
-    // a cell whose cost is not below it cannot set a bit of U(p, k-1) for p
-    // in the run, so its walk is skipped
+    // with the exact flag below it decides whether a cell can set a bit of
+    // U(p, k-1) for p in its run; cells that cannot skip the walk
     uint32_t rmax[kStrip / 2];
 #pragma unroll
     for (int q = 0; q < kStrip / 2; ++q) rmax[q] = 0xfc00fc00u;
+    // per cell, exactly: no earlier cost of the run exceeds the current one
+    // (constant and rising costs keep it; only then is the rounded bound needed)
+    uint32_t runle = 0xffu;
     auto rmax_get = [&](int q) -> float {
         const unsigned short hb = (unsigned short)(rmax[q >> 1] >> (16 * (q & 1)));
         return __half2float(__ushort_as_half(hb));
@@ -190,6 +193,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     // registers and leave with one atomic per word and warp.  Called by the
     // whole warp.
     auto mark_run = [&](uint32_t walk, int kk) {
+        if (!__any_sync(0xffffffffu, walk != 0)) return;
         uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;
         int lo = kk;
 #pragma unroll
@@ -509,7 +513,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
                 const int i = ty0 + tr0 + q;
                 const bool gq = (gchbits >> q) & 1u;
                 if (!first && i < a.H && j_out < a.W && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
-                    if (cT[q] < rmax_get(q)) walk |= 1u << q;
+                    if (!((runle >> q) & 1u)) walk |= 1u << q;
                     pre = max(pre, run_get(q) + 1);
                 }
             }
@@ -519,9 +523,15 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
                 if ((gchbits >> q) & 1u) {
                     run_set(q, k);
                     rmax_set(q, 0xfc00u);
+                    runle |= 1u << q;
                 } else if (!first) {
+                    // the run now covers slice k-1 (cost cT) and the current cost is acc:
+                    // max(run, cT) <= acc  <=  cT <= acc and (old flag or bound <= acc)
+                    const float mup = rmax_get(q);
+                    const bool le = cT[q] <= acc[q] && (((runle >> q) & 1u) || mup <= acc[q]);
+                    runle = le ? runle | (1u << q) : runle & ~(1u << q);
                     const __half hc = __float2half_ru(cT[q]);
-                    if (__half2float(hc) > rmax_get(q)) rmax_set(q, __half_as_ushort(hc));
+                    if (__half2float(hc) > mup) rmax_set(q, __half_as_ushort(hc));
                 }
                 cT[q] = acc[q];
             }
@@ -566,7 +576,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         for (int q = 0; q < kStrip; ++q) {
             const int i = ty0 + tr0 + q;
             if (i < a.H && j_out < a.W && cT[q] < c.c_b) {
-                if (cT[q] < rmax_get(q)) walk |= 1u << q;
+                if (!((runle >> q) & 1u)) walk |= 1u << q;
                 pre = max(pre, run_get(q) + 1);
             }
         }
