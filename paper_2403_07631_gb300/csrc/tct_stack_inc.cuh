@@ -342,7 +342,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
                                 eD > -INFINITY && eU > -INFINITY;
                 const float gx = (eR - eL) * c.inv2r;
                 const float gy = (eU - eD) * c.inv2r;
-                const bool gentle = ok && gx * gx + gy * gy < ts2 && gs < G::GW;
+                const bool gentle = ok && __fmaf_rn(gx, gx, __fmul_rn(gy, gy)) < ts2 && gs < G::GW;
                 const uint32_t bits = __ballot_sync(0xffffffffu, gentle);
                 if (lane == 0) {
                     const uint32_t old = sGB[gr * G::GWW + w];
@@ -407,54 +407,47 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             for (int t = warp; t < n_blk; t += kNW) {
                 const int blk = sList[t];
                 const int cr = blk / G::CPASS, w = blk - cr * G::CPASS;
+                // branch-free over the warp: every lane evaluates Eq. 1-5 with
+                // selects; p_s (Eq. 4) is counted when some lane needs it
                 const int cs = 32 * w + lane;
-                bool changed = false;
-                if (cs < G::CW) {
-                    const int i = ty0 - RK + cr, j = tx0 - RK + cs;
-                    float ci = 0.0f;                     // off-grid taps add nothing
-                    if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
-                        const int eidx = (cr + RP + 1) * G::EW + (cs + RP + 1);
-                        const float *ep = sEG + eidx;
-                        const float eg = ep[0];
-                        if (!(eg > -INFINITY)) {
-                            ci = c.c_b;
-                        } else {
-                            const float dI = sZC[eidx] - eg;
-                            float cI;
-                            if (dI < c.d_min) cI = c.c_b;
-                            else if (isinf(dI)) cI = 0.0f;
-                            else cI = fmaxf(0.0f, c.alpha_d * (c.d_ref - dI));
-                            const float eL = ep[-1], eR = ep[1], eD = ep[-G::EW], eU = ep[G::EW];
-                            float cg;
-                            if (!(eL > -INFINITY && eR > -INFINITY && eD > -INFINITY && eU > -INFINITY)) {
-                                cg = c.c_b;
-                            } else {
-                                const float gx = (eR - eL) * c.inv2r;
-                                const float gy = (eU - eD) * c.inv2r;
-                                const float m2 = gx * gx + gy * gy;
-                                const float mxy = fmaxf(fabsf(gx), fabsf(gy));
-                                if (mxy > c.theta_b) {
-                                    cg = c.c_b;
-                                } else if (m2 < ts2) {
-                                    cg = c.alpha_s * (m2 * inv_ts2);
-                                } else {
-                                    int count = 0;
-                                    const int w0 = cs >> 5, off = cs & 31;
+                const bool live = cs < G::CW;
+                const int csc = live ? cs : G::CW - 1;
+                const int i = ty0 - RK + cr, j = tx0 - RK + csc;
+                const bool in_map = live && i >= 0 && i < a.H && j >= 0 && j < a.W;
+                const int eidx = (cr + RP + 1) * G::EW + (csc + RP + 1);
+                const float *ep = sEG + eidx;
+                const float eg = ep[0], zc = sZC[eidx];
+                const float eL = ep[-1], eR = ep[1], eD = ep[-G::EW], eU = ep[G::EW];
+                const bool valid = eg > -INFINITY;
+                const float dI = zc - eg;
+                const float cI = dI < c.d_min ? c.c_b
+                                              : (isinf(dI) ? 0.0f : fmaxf(0.0f, c.alpha_d * (c.d_ref - dI)));
+                const bool ok = eL > -INFINITY && eR > -INFINITY && eD > -INFINITY && eU > -INFINITY;
+                const float gx = (eR - eL) * c.inv2r;
+                const float gy = (eU - eD) * c.inv2r;
+                const float m2 = __fmaf_rn(gx, gx, __fmul_rn(gy, gy));
+                const float mxy = fmaxf(fabsf(gx), fabsf(gy));
+                const bool barrier = !ok || mxy > c.theta_b;
+                const bool step = in_map && valid && !barrier && !(m2 < ts2);
+                float cg = barrier ? c.c_b : c.alpha_s * (m2 * inv_ts2);
+                if (__any_sync(0xffffffffu, step)) {
+                    int count = 0;
+                    const int w0 = csc >> 5, off = csc & 31;
 #pragma unroll
-                                    for (int dr = 0; dr <= 2 * RP; ++dr) {
-                                        const uint32_t *rowb = sGB + (cr + dr) * G::GWW;
-                                        const uint32_t bb = __funnelshift_r(rowb[w0], rowb[w0 + 1], off);
-                                        count += __popc(bb & ((1u << (2 * RP + 1)) - 1u));
-                                    }
-                                    const int cc = cs + RP;
-                                    count -= (sGB[(cr + RP) * G::GWW + (cc >> 5)] >> (cc & 31)) & 1u;
-                                    const float t = mxy * c.inv_tb;
-                                    cg = count > c.count_thresh ? c.alpha_b * (t * t) : c.c_b;
-                                }
-                            }
-                            ci = fminf(c.c_b, cI + cg);
-                        }
+                    for (int dr = 0; dr <= 2 * RP; ++dr) {
+                        const uint32_t *rowb = sGB + (cr + dr) * G::GWW;
+                        const uint32_t bb = __funnelshift_r(rowb[w0], rowb[w0 + 1], off);
+                        count += __popc(bb & ((1u << (2 * RP + 1)) - 1u));
                     }
+                    const int cc = csc + RP;
+                    count -= (sGB[(cr + RP) * G::GWW + (cc >> 5)] >> (cc & 31)) & 1u;
+                    const float t = mxy * c.inv_tb;
+                    if (step) cg = count > c.count_thresh ? c.alpha_b * (t * t) : c.c_b;
+                }
+                float ci = valid ? fminf(c.c_b, cI + cg) : c.c_b;
+                ci = in_map ? ci : 0.0f;              // off-grid taps add nothing
+                bool changed = false;
+                if (live) {
                     const int cidx = cr * G::CW + cs;
                     changed = first || __float_as_uint(ci) != __float_as_uint(sCI[cidx]);
                     sCI[cidx] = ci;
