@@ -592,7 +592,7 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
                           "peak_source": peak_src},
-        "roofline": {"kernel": "k_stack_batched<5,2,64,64> (per-tile incremental slice stack)", "bound": "hbm",
+        "roofline": {"kernel": "k_stack_batched<5,2> (per-tile incremental slice stack)", "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
                      "traffic": traffic, "algorithmic_bytes": sb, "ms": stack_ms,
                      "peak_source": peak_src},
