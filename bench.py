@@ -199,7 +199,7 @@ def cpu_baseline(sc, params, min_seconds=10.0, max_runs=20):
     oracle.compile_library()
     op = {k: params[k] for k in oracle.PARAM_FIELDS}
     runs = []
-    while len(runs) < max_runs and sum(runs) < min_seconds:
+    while not runs or (len(runs) < max_runs and sum(runs) < min_seconds):
         g = oracle.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, 0.0, sc.n_slices)
         t0 = time.perf_counter()
         eG, eC, g, _, _ = oracle.build(sc.points, g, True)
