@@ -346,6 +346,52 @@ def planned_paths(dev, grid, params, ground, cost, keep, stats, n_paths=256, L=5
     return out
 
 
+def small_map_graph(dev, params, steps):
+    """The two-storey building (200k points, 200 x 200 x 12): a map this small
+    is launch-bound, so beside the plain call it is timed as a replay of a
+    CUDA graph that captured the call."""
+    import torch
+    from paper_2403_07631_gb300 import tct
+    sc = workload("building")
+    grid = tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, sc.n_slices, 0.0, True)
+    pts = torch.from_numpy(sc.points).to(dev)
+    bufs = tct.alloc_outputs(grid, len(sc.points), dev, params)
+    stream = torch.cuda.current_stream()
+    tct.tct_timing_enable(False)
+
+    def call():
+        tct.tct_build_evaluate(pts, grid, params, *bufs)
+
+    def timed(fn, n):
+        out = []
+        for i in range(n + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if i >= 3:
+                out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    t_plain = timed(call, steps)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        call()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        call()
+    t_graph = timed(graph.replay, steps)
+    tct.tct_timing_enable(True)          # the later measurements read the phase times
+    P, SC = len(sc.points), sc.n_slices * sc.H * sc.W
+    return {"workload": sc.name, "plain_us": t_plain * 1e3, "graph_replay_us": t_graph * 1e3,
+            "graph_speedup": t_plain / t_graph, "mpoints_per_s_graph": P / (t_graph * 1e-3) / 1e6,
+            "slice_cells_per_s_graph": SC / (t_graph * 1e-3)}
+
+
 def batched_vs_plain(dev, params, steps):
     """64 maps of uneven size (points log-uniform 50k-4M, sides 128-1024 cells,
     4-48 slices): sequential single-map calls against one batched call (tuned by
@@ -602,8 +648,11 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "kept_slices": int(st.n_kept),
+        "valid_frac_per_slice": [round(st.valid_cells[k] / (H * W), 4) for k in range(N)],
+        "trav_frac_per_slice": [round(st.trav_cells[k] / (H * W), 4) for k in range(N)],
     }
     out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
+    out["small_map"] = small_map_graph(dev, params, args.steps)
     if not args.no_planner:
         out["planned_paths"] = planned_paths(dev, grid, params, ground, cost, keep, stats)
     if not args.no_batched:

@@ -15,13 +15,13 @@
  *     (the host-side planner keeps its own host tables).
  *   - Calls are asynchronous on `stream` (NULL = the legacy default stream)
  *     and perform no host synchronisation, so a sequence of calls can be
- *     captured into a CUDA graph.
+ *     captured into a CUDA graph (tct_get_status and the autotuner excepted).
  *   - Layered outputs are dense [n_slices][H][W] row-major; row i runs along
  *     +y (cell i covers [y0 + i*res, y0 + (i+1)*res)), column j along +x.
  *   - Return value: TCT_OK (0) or a negative TCT_ERR_* code for errors the
  *     host can see (bad arguments, too small a workspace, a failed launch).
  *     Errors only the device can see (non-finite points) are OR-ed into
- *     tct_stats.status; read the stats after synchronising the stream.
+ *     tct_stats.status; tct_get_status reads it at a sync point.
  *   - Invalid elevations: ground -inf, ceiling +inf (Sec. III-A: a cell with
  *     no point in the group is invalid).
  */
@@ -110,6 +110,15 @@ const char *tct_status_string(int status);
 
 /* ABI version (major * 10000 + minor * 100 + patch). */
 int tct_version(void);
+
+/*
+ * The sync point for device-detected errors: copies d_stats->status (an OR of
+ * TCT_DEV_* bits written by the calls queued before it) to *h_status and
+ * waits for `stream`.  The one entry point that synchronises; it does not
+ * belong in a captured graph.  TCT_ERR_INVALID_ARG for NULL pointers,
+ * TCT_ERR_CUDA when the copy or the stream failed (a launch error included).
+ */
+int tct_get_status(const tct_stats *d_stats, int32_t *h_status, tct_stream stream);
 
 /*
  * Table I defaults (d_min 0.5, d_ref 0.65, theta_b 1.70, theta_s 0.36,

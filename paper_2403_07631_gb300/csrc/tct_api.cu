@@ -167,6 +167,16 @@ const char *tct_status_string(int status) {
 
 int tct_version(void) { return 10000; }
 
+int tct_get_status(const tct_stats *d_stats, int32_t *h_status, tct_stream stream) {
+    if (!d_stats || !h_status) return TCT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h_status, &d_stats->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return TCT_ERR_CUDA;
+    return TCT_OK;
+}
+
 void tct_params_default(tct_params *p) {
     if (!p) return;
     p->d_min = 0.50f;

@@ -109,6 +109,7 @@ _SIGNATURES = {
     "tct_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
+    "tct_get_status": (ctypes.c_int, [_P, _P, _P]),
     "tct_planner_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "tct_planner_destroy": (None, [_P]),
@@ -447,6 +448,15 @@ def alloc_outputs(grid: Grid, n_points: int, device="cuda", params: dict | None 
     keep = torch.empty(grid.n_slices, dtype=torch.uint8, device=device)
     stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
     return ws, ground, ceil, cost, mask, keep, stats
+
+
+def tct_get_status(stats: torch.Tensor) -> int:
+    """The device status word (TCT_DEV_* bits) of a stats block, at a sync
+    point on the current stream."""
+    out = ctypes.c_int32(0)
+    _check("tct_get_status", load().tct_get_status(_ptr(stats), ctypes.byref(out),
+                                                   _stream()))
+    return out.value
 
 
 def tct_timing_enable(on: bool = True):

@@ -100,6 +100,22 @@ def test_build_nonfinite_and_offgrid_points():
     assert not np.any((ground == 0) & np.signbit(ground))     # -0 is stored as +0
 
 
+def test_get_status_reads_the_device_word():
+    pts = np.zeros((64, 3), np.float32)
+    pts[:, :2] = 0.5
+    grid = tct.Grid(0.0, 0.0, 0.1, 20, 20, 0.5, 4, 0.0, True)
+    d = torch.from_numpy(pts).cuda()
+    ws = torch.empty(tct.tct_workspace_bytes(grid, len(pts)), dtype=torch.uint8, device="cuda")
+    g = torch.empty(grid.shape, device="cuda")
+    c = torch.empty(grid.shape, device="cuda")
+    stats = torch.zeros(tct.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    tct.tct_build(d, grid, ws, g, c, stats)
+    assert tct.tct_get_status(stats) == 0
+    d[3, 1] = float("nan")
+    tct.tct_build(d, grid, ws, g, c, stats)
+    assert tct.tct_get_status(stats) & tct.DEV_NONFINITE
+
+
 def test_build_empty_cloud():
     pts = np.zeros((0, 3), np.float32)
     grid = tct.Grid(0.0, 0.0, 0.1, 20, 10, 0.5, 3, 0.0, False)
