@@ -149,3 +149,29 @@ def test_batch_refusals():
         tct.tct_build_evaluate_batched([maps[0], other], PARAMS_ROBOT, ws)
     with pytest.raises(tct.TctError, match="limit"):
         tct.tct_build_evaluate_batched(maps, dict(PARAMS_ROBOT, patch_radius=3), ws)
+
+
+@pytest.mark.parametrize("res,params", [(0.1, PARAMS_TABLE1), (0.05, PARAMS_ROBOT)])
+@pytest.mark.parametrize("tile", [tct.TILE_64x56, tct.TILE_64, tct.TILE_32])
+def test_batch_other_window_radii(res, params, tile):
+    """The radius-4 (Table I, 0.1 m) and radius-12 (0.05 m) instances in every
+    tile shape, on maps with ragged last tiles."""
+    rng = np.random.default_rng(11)
+    scs = []
+    for i, side in enumerate((70, 131, 97)):
+        sc = scenes.building(300 + i, int(rng.integers(20_000, 60_000)), side, res, [0.0, 1.1],
+                             [0.9, 2.4], 8.0, 0.01)
+        sc.n_slices = int(rng.integers(3, 9))
+        scs.append(sc)
+    maps = _maps(scs)
+    ws = torch.empty(tct.tct_workspace_bytes_batched(maps, params), dtype=torch.uint8,
+                     device="cuda")
+    tct.tct_build_evaluate_batched(maps, params, ws, tct.TctTuning(tile, 0, 4096, 0))
+    torch.cuda.synchronize()
+    for sc, m in zip(scs, maps):
+        got = _host(m)
+        ref = P.oracle_all(sc.points, _grid(sc), params)
+        P.assert_equal_layers(got["ground"], ref["ground"], "ground")
+        P.assert_costs(got["cost"], ref["cost"], ref["fragile"])
+        P.assert_masks(got["mask"], ref["mask"], ref["fragile"])
+        P.assert_keep(got["keep"], got["ground"], got["cost"], ref, params)
