@@ -191,6 +191,38 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
                        float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
                        uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
 
+/* ---- host buffers in, host buffers out --------------------------------- */
+
+#define TCT_HOST_KEPT_ONLY 1u          /* return only the slices the simplification kept */
+
+/* The host side of tct_build_evaluate_host; host arrays, pinned for asynchronous copies. */
+typedef struct tct_host_io {
+    const float *h_xyz;                  /* n points, `stride` floats apart           */
+    float *h_ground, *h_ceil, *h_cost;   /* [N][H][W] or [M][H][W]; any may be NULL    */
+    uint8_t *h_mask;                     /* likewise; may be NULL                      */
+    uint8_t *h_keep;                     /* [N]; needed with TCT_HOST_KEPT_ONLY        */
+    uint32_t flags;                      /* TCT_HOST_*                                 */
+    int32_t n_kept;                      /* out: M, the slices copied (N without KEPT_ONLY) */
+} tct_host_io;
+
+/*
+ * tct_build_evaluate from host memory to host memory: copies the cloud into
+ * d_xyz (device staging of n * stride floats), runs the fused path into the
+ * caller's device layers and copies the layers back, one cudaMemcpyAsync
+ * per copy, all on `stream`.  Without TCT_HOST_KEPT_ONLY nothing waits: the
+ * host arrays are complete when the stream is, and calls on two streams with
+ * two sets of buffers overlap one map's copies with the next map's work.
+ * With TCT_HOST_KEPT_ONLY the call reads the keep flags (it waits for the
+ * stream once), then copies only the kept slices, packed in slice order into
+ * [M][H][W] (the simplified tomogram of Sec. III-C) and sets io->n_kept = M.
+ * Errors as tct_build_evaluate; TCT_ERR_INVALID_ARG also for a NULL io,
+ * h_xyz (n > 0), d_xyz, or h_keep with TCT_HOST_KEPT_ONLY.
+ */
+int tct_build_evaluate_host(tct_host_io *io, int64_t n, int32_t stride, const tct_grid *grid,
+                            const tct_params *params, void *d_ws, size_t ws_bytes, float *d_xyz,
+                            float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
+                            uint8_t *d_keep, tct_stats *d_stats, tct_stream stream);
+
 /* ---- queries (Sec. III-E, Eq. 10: C(q), e^G(q)) ------------------------- */
 
 /*

@@ -317,6 +317,52 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
     return cuda_status(e);
 }
 
+int tct_build_evaluate_host(tct_host_io *io, int64_t n, int32_t stride, const tct_grid *grid,
+                            const tct_params *params, void *d_ws, size_t ws_bytes, float *d_xyz,
+                            float *d_ground, float *d_ceil, float *d_cost, uint8_t *d_mask,
+                            uint8_t *d_keep, tct_stats *d_stats, tct_stream stream) {
+    if (!io || !grid_ok(grid) || !d_xyz || (n > 0 && !io->h_xyz)) return TCT_ERR_INVALID_ARG;
+    if ((stride != 3 && stride != 4) || n < 0 || n > TCT_MAX_POINTS) return TCT_ERR_INVALID_ARG;
+    const bool kept_only = (io->flags & TCT_HOST_KEPT_ONLY) != 0;
+    if (kept_only && !io->h_keep) return TCT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n > 0 && cudaMemcpyAsync(d_xyz, io->h_xyz, sizeof(float) * (size_t)n * stride,
+                                 cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TCT_ERR_CUDA;
+    int rc = tct_build_evaluate(d_xyz, n, stride, grid, params, d_ws, ws_bytes, d_ground, d_ceil,
+                                d_cost, d_mask, d_keep, d_stats, stream);
+    if (rc != TCT_OK) return rc;
+    const int N = grid->n_slices;
+    const size_t hw = (size_t)grid->W * grid->H;
+    // the layers with a host destination: (device, host, bytes per cell)
+    struct Layer { const void *d; void *h; size_t es; } layers[4] = {
+        {d_ground, io->h_ground, 4}, {d_ceil, io->h_ceil, 4}, {d_cost, io->h_cost, 4},
+        {d_mask, io->h_mask, 1}};
+    cudaError_t e = cudaSuccess;
+    if (io->h_keep)
+        e = cudaMemcpyAsync(io->h_keep, d_keep, (size_t)N, cudaMemcpyDeviceToHost, s);
+    if (!kept_only) {
+        for (const Layer &L : layers)
+            if (L.h && e == cudaSuccess)
+                e = cudaMemcpyAsync(L.h, L.d, L.es * hw * N, cudaMemcpyDeviceToHost, s);
+        io->n_kept = N;
+        return e == cudaSuccess ? TCT_OK : TCT_ERR_CUDA;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int m = 0;
+    for (int k = 0; k < N && e == cudaSuccess; ++k) {
+        if (!io->h_keep[k]) continue;
+        for (const Layer &L : layers)
+            if (L.h && e == cudaSuccess)
+                e = cudaMemcpyAsync(static_cast<uint8_t *>(L.h) + L.es * hw * m,
+                                    static_cast<const uint8_t *>(L.d) + L.es * hw * k, L.es * hw,
+                                    cudaMemcpyDeviceToHost, s);
+        ++m;
+    }
+    io->n_kept = m;
+    return e == cudaSuccess ? TCT_OK : TCT_ERR_CUDA;
+}
+
 int tct_timing_enable(int on) {
     if (on && !g_timing.created) {
         for (int i = 0; i < 4; ++i)

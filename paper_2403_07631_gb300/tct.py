@@ -66,6 +66,16 @@ class TctMap(ctypes.Structure):
                 ("d_keep", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
 
 
+class TctHostIO(ctypes.Structure):
+    _fields_ = [("h_xyz", ctypes.c_void_p), ("h_ground", ctypes.c_void_p),
+                ("h_ceil", ctypes.c_void_p), ("h_cost", ctypes.c_void_p),
+                ("h_mask", ctypes.c_void_p), ("h_keep", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("n_kept", ctypes.c_int32)]
+
+
+HOST_KEPT_ONLY = 1
+
+
 class TctTuning(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("points_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -110,6 +120,10 @@ _SIGNATURES = {
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
     "tct_get_status": (ctypes.c_int, [_P, _P, _P]),
+    "tct_build_evaluate_host": (ctypes.c_int, [ctypes.POINTER(TctHostIO), ctypes.c_int64,
+                                               ctypes.c_int32, ctypes.POINTER(TctGrid),
+                                               ctypes.POINTER(TctParams), _P, ctypes.c_size_t, _P,
+                                               _P, _P, _P, _P, _P, _P, _P]),
     "tct_planner_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "tct_planner_destroy": (None, [_P]),
@@ -448,6 +462,29 @@ def alloc_outputs(grid: Grid, n_points: int, device="cuda", params: dict | None 
     keep = torch.empty(grid.n_slices, dtype=torch.uint8, device=device)
     stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
     return ws, ground, ceil, cost, mask, keep, stats
+
+
+def tct_build_evaluate_host(h_xyz: torch.Tensor, grid: Grid, params: dict, ws: torch.Tensor,
+                            d_xyz: torch.Tensor, ground: torch.Tensor, ceil: torch.Tensor,
+                            cost: torch.Tensor, mask: torch.Tensor, keep: torch.Tensor,
+                            stats: torch.Tensor | None = None, h_ground=None, h_ceil=None,
+                            h_cost=None, h_mask=None, h_keep=None, kept_only: bool = False) -> int:
+    """Host cloud in, host layers out (pinned CPU tensors for asynchronous
+    copies), through the caller's device buffers, on the current stream.
+    Returns the number of slices copied (the kept ones with kept_only)."""
+    if h_xyz.is_cuda or d_xyz.shape != h_xyz.shape:
+        raise ValueError("h_xyz must be a host tensor shaped like d_xyz")
+    n, stride = _points(h_xyz)
+    io = TctHostIO(_ptr(h_xyz), _ptr(h_ground), _ptr(h_ceil), _ptr(h_cost), _ptr(h_mask),
+                   _ptr(h_keep), HOST_KEPT_ONLY if kept_only else 0, 0)
+    cp = _params_c(params)
+    _check("tct_build_evaluate_host",
+           load().tct_build_evaluate_host(ctypes.byref(io), n, stride, ctypes.byref(grid.c()),
+                                          ctypes.byref(cp), _ptr(ws),
+                                          ws.numel() * ws.element_size(), _ptr(d_xyz),
+                                          _ptr(ground), _ptr(ceil), _ptr(cost), _ptr(mask),
+                                          _ptr(keep), _ptr(stats), _stream()))
+    return io.n_kept
 
 
 def tct_get_status(stats: torch.Tensor) -> int:

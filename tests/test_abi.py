@@ -50,6 +50,35 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(tct.TctStats) == 48 + 2 * 8 * 128
 
 
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every struct of the header, compiled by the host C compiler: the same
+    size and the same offset of every field as the binding's ctypes types."""
+    import shutil
+    import subprocess
+    from paper_2403_07631_gb300 import tct
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    types = {"tct_grid": tct.TctGrid, "tct_params": tct.TctParams, "tct_stats": tct.TctStats,
+             "tct_map": tct.TctMap, "tct_tuning": tct.TctTuning, "tct_host_io": tct.TctHostIO}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tct.h"', 'int main(void) {']
+    for cname, ct in types.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in ct._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, what, value = line.split()
+        ct = types[cname]
+        got = ctypes.sizeof(ct) if what == "size" else getattr(ct, what).offset
+        assert got == int(value), f"{cname}.{what}: binding {got}, C {value}"
+
+
 def test_host_only_calls(lib):
     from paper_2403_07631_gb300 import tct
     assert tct.tct_status_string(0) == "ok"

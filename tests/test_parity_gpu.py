@@ -280,3 +280,26 @@ def test_long_cell_segments():
     pts = np.concatenate([base] + cols).astype(np.float32)
     grid = tct.Grid(0.0, 0.0, 0.1, 40, 40, 0.5, 13, 0.0, True)
     _full_check(pts, grid, PARAMS_ROBOT)
+
+
+@pytest.mark.parametrize("kept_only", [False, True])
+def test_host_buffers_entry_point(kept_only):
+    sc = scenes.building(41, 60_000, 90, 0.1, [0.0, 1.6], [1.4, 3.2], 6.0, 0.01)
+    grid = tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, 9, 0.0, True)
+    ref = P.gpu_build_evaluate(sc.points, grid, PARAMS_ROBOT)
+    h_xyz = torch.from_numpy(sc.points).pin_memory()
+    d_xyz = torch.empty_like(h_xyz, device="cuda")
+    ws, g, c, cost, mask, keep, stats = tct.alloc_outputs(grid, len(sc.points), "cuda",
+                                                          PARAMS_ROBOT)
+    hs = [torch.full(grid.shape, -7.0).pin_memory() for _ in range(3)]
+    hm = torch.full(grid.shape, 9, dtype=torch.uint8).pin_memory()
+    hk = torch.zeros(grid.n_slices, dtype=torch.uint8).pin_memory()
+    m = tct.tct_build_evaluate_host(h_xyz, grid, PARAMS_ROBOT, ws, d_xyz, g, c, cost, mask, keep,
+                                    stats, hs[0], hs[1], hs[2], hm, hk, kept_only=kept_only)
+    torch.cuda.synchronize()
+    k = np.flatnonzero(ref["keep"]) if kept_only else np.arange(grid.n_slices)
+    assert m == len(k) and np.array_equal(hk.numpy(), ref["keep"])
+    for h, key in zip(hs + [hm], ("ground", "ceil", "cost", "mask")):
+        np.testing.assert_array_equal(h.numpy()[:m], ref[key][k], err_msg=key)
+    if kept_only:   # beyond the kept slices the host arrays are untouched
+        assert (hs[2].numpy()[m:] == -7.0).all() and (hm.numpy()[m:] == 9).all()
