@@ -212,6 +212,34 @@ __device__ __forceinline__ void visit_point(float x, float y, float z, const Gri
     }
 }
 
+// Pass 2 for four points at once, in phases: the four slot atomics, then the
+// four segment starts, then the four stores, so that the round trips of the
+// four points overlap instead of following one another.
+__device__ __forceinline__ void scatter4(const float (&p)[4][3], const GridDev &g, int64_t cell_off,
+                                         int32_t *__restrict__ cnt,
+                                         const int32_t *__restrict__ start,
+                                         float *__restrict__ zs) {
+    int64_t gc[4];
+    float z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        gc[u] = -1;
+        z[u] = fold_zero(p[u][2]);
+        if (finite3(p[u][0], p[u][1], p[u][2])) {
+            const int cell = cell_of(g, p[u][0], p[u][1]);
+            if (cell >= 0) gc[u] = cell_off + cell;
+        }
+    }
+    int32_t slot[4], base[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) slot[u] = gc[u] >= 0 ? cell_slot<true>(cnt, gc[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) base[u] = gc[u] >= 0 ? start[gc[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (gc[u] >= 0) zs[base[u] + slot[u]] = z[u];
+}
+
 // Points [p0, p1) of one map, thread `tid` of `nthreads`: groups of four
 // with vector loads where the base allows, the ragged ends one by one.
 template <bool kScatter>
@@ -230,9 +258,13 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
     for (int64_t q = q0 + tid; q < q1; q += nthreads) {
         float p[4][3];
         load4(xyz, stride, q, p);
+        if (kScatter) {
+            scatter4(p, g, cell_off, cnt, start, zs);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            visit_point<kScatter>(p[u][0], p[u][1], p[u][2], g, cell_off, cnt, start, zs, t);
+            for (int u = 0; u < 4; ++u)
+                visit_point<false>(p[u][0], p[u][1], p[u][2], g, cell_off, cnt, start, zs, t);
+        }
     }
     const int64_t a1 = vec ? min(4 * q0, p1) : p1;
     for (int64_t i = p0 + tid; i < a1; i += nthreads) {
