@@ -682,6 +682,10 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "kept_slices": int(st.n_kept),
+        "paper_context": {"hardware": "RTX 3080 Ti + i9-12900KF (Table III)",
+                          "build_plus_eval_ms": "4.4-32.5 on the paper's scenes",
+                          "slice_cells_per_s": "about 0.2-0.7 G/s (derived; point counts not given)",
+                          "note": "other hardware and scenes: context, not the target"},
         "valid_frac_per_slice": [round(st.valid_cells[k] / (H * W), 4) for k in range(N)],
         "trav_frac_per_slice": [round(st.trav_cells[k] / (H * W), 4) for k in range(N)],
     }
