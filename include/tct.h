@@ -309,6 +309,34 @@ int tct_build_evaluate_batched(const tct_map *h_maps, int32_t n_maps, const tct_
                                tct_stream stream);
 
 /*
+ * The construction alone (tct_build) for up to TCT_MAX_BATCH maps: the two
+ * point passes over all clouds together, then one launch that walks every
+ * cell of every map up its slices; writes each map's d_ground and d_ceil
+ * (d_cost, d_mask and d_keep are not used and may be NULL) and its stats
+ * (points, dropped, non-finite, z bounds).  The workspace is that of
+ * tct_workspace_bytes_batched (params may be NULL there); tuning may be
+ * NULL, only its points_per_block is used.  Graph-capturable.  Each map's
+ * layers are those of tct_build on that map alone.
+ */
+int tct_build_batched(const tct_map *h_maps, int32_t n_maps, const tct_tuning *tuning,
+                      void *d_ws, size_t ws_bytes, tct_stream stream);
+
+/* Workspace of tct_evaluate_batched: the largest tct_evaluate workspace of the maps. */
+size_t tct_workspace_bytes_evaluate_batched(const tct_map *h_maps, int32_t n_maps,
+                                            const tct_params *params);
+
+/*
+ * The evaluation alone (tct_evaluate) for up to TCT_MAX_BATCH maps whose
+ * d_ground / d_ceil already hold layers: writes each map's d_cost, d_mask,
+ * d_keep and stats.  The maps run one after another on `stream`, reusing one
+ * workspace (an evaluation reads no points, so there is nothing to merge);
+ * each map's outputs are those of tct_evaluate on that map alone.  The first
+ * failing map's status is returned and the maps after it are not run.
+ */
+int tct_evaluate_batched(const tct_map *h_maps, int32_t n_maps, const tct_params *params,
+                         void *d_ws, size_t ws_bytes, tct_stream stream);
+
+/*
  * Times tct_build_evaluate_batched on this batch for each candidate tuning
  * (tile shape, persistent CTAs per SM, points per block) and writes the
  * fastest into *out.  Runs the batch several times (the outputs are written)

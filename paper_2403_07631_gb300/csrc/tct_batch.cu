@@ -228,10 +228,183 @@ tct_tuning default_tuning() {
     return t;
 }
 
+// The construction alone for a batch: one thread per cell of all maps walks
+// the slices with the monotone pointer (as tct_build does for one map).
+struct ElevBatch {
+    int32_t n_maps;
+    int64_t cell_start[TCT_MAX_BATCH + 1];   // first cell of each map in the concatenation
+    struct {
+        int32_t N, zmin_from_data;
+        float d_s, z_min;
+        const int32_t *zkeys;
+        float *ground, *ceil;
+    } m[TCT_MAX_BATCH];
+};
+
+__global__ void __launch_bounds__(256)
+k_elevations_batched(const __grid_constant__ ElevBatch b, const int32_t *__restrict__ start,
+                     const float *__restrict__ zs) {
+    const int64_t total = b.cell_start[b.n_maps];
+    for (int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gc < total;
+         gc += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = b.n_maps - 1;           // the map holding cell gc
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.cell_start[mid] <= gc) lo = mid;
+            else hi = mid - 1;
+        }
+        const auto &m = b.m[lo];
+        const int64_t c = gc - b.cell_start[lo];
+        const int64_t hw = b.cell_start[lo + 1] - b.cell_start[lo];
+        float z_min = m.z_min;
+        if (m.zmin_from_data) {
+            z_min = key_float(m.zkeys[0]);
+            if (!isfinite(z_min)) z_min = 0.0f;
+        }
+        int32_t p = start[gc];
+        const int32_t e = start[gc + 1];
+        float zg = -INFINITY;
+        float zc = p < e ? zs[p] : INFINITY;
+        for (int k = 0; k < m.N; ++k) {
+            const float h = __fmaf_rn((float)(k + 1), m.d_s, z_min);
+            while (zc <= h) {
+                zg = zc;
+                ++p;
+                zc = p < e ? zs[p] : INFINITY;
+            }
+            __stcs(&m.ground[(int64_t)k * hw + c], zg);
+            __stcs(&m.ceil[(int64_t)k * hw + c], zc);
+        }
+    }
+}
+
+// z bounds of each map into its statistics (the construction-only batch).
+__global__ void k_batch_bounds(const __grid_constant__ BatchSmall b) {
+    const auto &m = b.m[blockIdx.x];
+    if (threadIdx.x == 0) {
+        m.stats->z_min = key_float(m.zkeys[0]);
+        m.stats->z_max = key_float(m.zkeys[1]);
+    }
+}
+
+int run_build_batch(const tct_map *maps, int n_maps, int points_per_block, void *d_ws,
+                    cudaStream_t s) {
+    const BatchLayout L = batch_layout(maps, n_maps);
+    char *base = static_cast<char *>(d_ws);
+    Workspace ws;
+    memset(&ws, 0, sizeof(ws));
+    ws.cnt = reinterpret_cast<int32_t *>(base + L.cnt);
+    ws.start = reinterpret_cast<int32_t *>(base + L.start);
+    ws.partial = reinterpret_cast<int32_t *>(base + L.partial);
+    ws.zs = reinterpret_cast<float *>(base + L.zs);
+    ws.scratch = reinterpret_cast<float *>(base + L.scratch);
+    ws.long_count = reinterpret_cast<int32_t *>(base + L.long_count);
+    ws.long_cells = reinterpret_cast<int32_t *>(base + L.long_cells);
+    int32_t *zkeys = reinterpret_cast<int32_t *>(base + L.zkeys);
+    tct_stats *stats = reinterpret_cast<tct_stats *>(base + L.stats);
+    BatchSmall small;
+    memset(&small, 0, sizeof(small));
+    small.n_maps = n_maps;
+    small.queue = reinterpret_cast<int32_t *>(base + L.queue);
+    ElevBatch eb;
+    memset(&eb, 0, sizeof(eb));
+    eb.n_maps = n_maps;
+    std::vector<BatchPointsIn> pin(n_maps);
+    int64_t cell_off = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        const tct_map &m = maps[i];
+        auto &sm = small.m[i];
+        sm.zkeys = zkeys + 2 * i;
+        sm.upre = reinterpret_cast<int32_t *>(base + L.upre) + (TCT_MAX_SLICES + 1) * i;
+        sm.ubits = reinterpret_cast<uint32_t *>(base + L.ubits) + 4 * (TCT_MAX_SLICES + 1) * i;
+        sm.stats = m.d_stats ? m.d_stats : stats + i;
+        sm.n_points = m.n;
+        sm.n_slices = m.grid.n_slices;
+        pin[i] = BatchPointsIn{m.d_xyz, m.n, m.stride, m.grid, cell_off, sm.zkeys, sm.stats};
+        eb.cell_start[i] = cell_off;
+        eb.m[i].N = m.grid.n_slices;
+        eb.m[i].zmin_from_data = (m.grid.flags & TCT_GRID_ZMIN_FROM_DATA) ? 1 : 0;
+        eb.m[i].d_s = m.grid.d_s;
+        eb.m[i].z_min = m.grid.z_min;
+        eb.m[i].zkeys = sm.zkeys;
+        eb.m[i].ground = m.d_ground;
+        eb.m[i].ceil = m.d_ceil;
+        cell_off += (int64_t)m.grid.W * m.grid.H;
+    }
+    eb.cell_start[n_maps] = cell_off;
+    k_batch_init<<<n_maps, 256, 0, s>>>(small);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_partition_batched(pin.data(), n_maps, points_per_block, L.cells, ws, s);
+    if (e == cudaSuccess) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (cell_off + 255) / 256;
+        if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+        if (blocks < 1) blocks = 1;
+        k_elevations_batched<<<(unsigned)blocks, 256, 0, s>>>(eb, ws.start, ws.zs);
+        k_batch_bounds<<<n_maps, 32, 0, s>>>(small);
+        count_launches(2);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? TCT_OK : TCT_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace tct
 
 using namespace tct;
+
+extern "C" int tct_build_batched(const tct_map *h_maps, int32_t n_maps, const tct_tuning *tuning,
+                                 void *d_ws, size_t ws_bytes, tct_stream stream) {
+    if (!h_maps || n_maps < 1 || !d_ws) return TCT_ERR_INVALID_ARG;
+    if (n_maps > TCT_MAX_BATCH) return TCT_ERR_UNSUPPORTED;
+    int64_t cells = 0, points = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        const tct_map &m = h_maps[i];
+        if (tct_workspace_bytes(&m.grid, m.n, nullptr) == 0) return TCT_ERR_INVALID_ARG;
+        if (m.grid.n_slices > TCT_MAX_SLICES) return TCT_ERR_UNSUPPORTED;
+        if ((m.stride != 3 && m.stride != 4) || (m.n > 0 && !m.d_xyz)) return TCT_ERR_INVALID_ARG;
+        if (!m.d_ground || !m.d_ceil) return TCT_ERR_INVALID_ARG;
+        cells += (int64_t)m.grid.W * m.grid.H;
+        points += m.n;
+    }
+    if (cells >= ((int64_t)1 << 31) || points >= ((int64_t)1 << 31)) return TCT_ERR_UNSUPPORTED;
+    if (ws_bytes < batch_layout(h_maps, n_maps).total) return TCT_ERR_WORKSPACE_TOO_SMALL;
+    const int ppb = tuning ? tuning->points_per_block : default_tuning().points_per_block;
+    if (ppb < 4 || ppb % 4) return TCT_ERR_INVALID_ARG;
+    return run_build_batch(h_maps, n_maps, ppb, d_ws, (cudaStream_t)stream);
+}
+
+extern "C" size_t tct_workspace_bytes_evaluate_batched(const tct_map *h_maps, int32_t n_maps,
+                                                       const tct_params *params) {
+    if (!h_maps || n_maps < 1 || n_maps > TCT_MAX_BATCH) return 0;
+    size_t most = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        const size_t b = tct_workspace_bytes(&h_maps[i].grid, 0, params);
+        if (b == 0) return 0;
+        most = std::max(most, b);
+    }
+    return most;
+}
+
+extern "C" int tct_evaluate_batched(const tct_map *h_maps, int32_t n_maps, const tct_params *params,
+                                    void *d_ws, size_t ws_bytes, tct_stream stream) {
+    if (!h_maps || n_maps < 1 || !params || !d_ws) return TCT_ERR_INVALID_ARG;
+    if (n_maps > TCT_MAX_BATCH) return TCT_ERR_UNSUPPORTED;
+    const size_t need = tct_workspace_bytes_evaluate_batched(h_maps, n_maps, params);
+    if (need == 0) return TCT_ERR_INVALID_ARG;
+    if (ws_bytes < need) return TCT_ERR_WORKSPACE_TOO_SMALL;
+    for (int i = 0; i < n_maps; ++i) {
+        const tct_map &m = h_maps[i];
+        const int rc = tct_evaluate(&m.grid, params, m.d_ground, m.d_ceil, d_ws, ws_bytes, m.d_cost,
+                                    m.d_mask, m.d_keep, nullptr, m.d_stats, stream);
+        if (rc != TCT_OK) return rc;
+    }
+    return TCT_OK;
+}
 
 extern "C" size_t tct_workspace_bytes_batched(const tct_map *h_maps, int32_t n_maps,
                                               const tct_params *params) {

@@ -120,6 +120,13 @@ _SIGNATURES = {
     "tct_timing_read": (ctypes.c_int, [_P, ctypes.c_int]),
     "tct_launch_count": (ctypes.c_int64, []),
     "tct_get_status": (ctypes.c_int, [_P, _P, _P]),
+    "tct_build_batched": (ctypes.c_int, [ctypes.POINTER(TctMap), ctypes.c_int32,
+                                         ctypes.POINTER(TctTuning), _P, ctypes.c_size_t, _P]),
+    "tct_workspace_bytes_evaluate_batched": (ctypes.c_size_t, [ctypes.POINTER(TctMap),
+                                                               ctypes.c_int32,
+                                                               ctypes.POINTER(TctParams)]),
+    "tct_evaluate_batched": (ctypes.c_int, [ctypes.POINTER(TctMap), ctypes.c_int32,
+                                            ctypes.POINTER(TctParams), _P, ctypes.c_size_t, _P]),
     "tct_build_evaluate_host": (ctypes.c_int, [ctypes.POINTER(TctHostIO), ctypes.c_int64,
                                                ctypes.c_int32, ctypes.POINTER(TctGrid),
                                                ctypes.POINTER(TctParams), _P, ctypes.c_size_t, _P,
@@ -430,6 +437,33 @@ def tct_build_evaluate_batched(maps: list[MapBuffers], params: dict, ws: torch.T
            load().tct_build_evaluate_batched(arr, len(maps), ctypes.byref(cp),
                                              ctypes.byref(tuning) if tuning is not None else None,
                                              _ptr(ws), ws.numel() * ws.element_size(), _stream()))
+
+
+def tct_build_batched(maps: list[MapBuffers], ws: torch.Tensor, tuning: TctTuning | None = None):
+    """Ground and ceiling layers of every map (the construction alone)."""
+    arr = _maps_c(maps)
+    _check("tct_build_batched",
+           load().tct_build_batched(arr, len(maps),
+                                    ctypes.byref(tuning) if tuning is not None else None,
+                                    _ptr(ws), ws.numel() * ws.element_size(), _stream()))
+
+
+def tct_workspace_bytes_evaluate_batched(maps: list[MapBuffers], params: dict) -> int:
+    arr = _maps_c(maps)
+    cp = _params_c(params)
+    n = load().tct_workspace_bytes_evaluate_batched(arr, len(maps), ctypes.byref(cp))
+    if n == 0:
+        raise TctError("tct_workspace_bytes_evaluate_batched", -1)
+    return n
+
+
+def tct_evaluate_batched(maps: list[MapBuffers], params: dict, ws: torch.Tensor):
+    """Costs, masks and keep flags of every map from the layers in its ground / ceil."""
+    arr = _maps_c(maps)
+    cp = _params_c(params)
+    _check("tct_evaluate_batched",
+           load().tct_evaluate_batched(arr, len(maps), ctypes.byref(cp), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream()))
 
 
 def tct_autotune_batched(maps: list[MapBuffers], params: dict, ws: torch.Tensor) -> TctTuning:

@@ -175,3 +175,34 @@ def test_batch_other_window_radii(res, params, tile):
         P.assert_costs(got["cost"], ref["cost"], ref["fragile"])
         P.assert_masks(got["mask"], ref["mask"], ref["fragile"])
         P.assert_keep(got["keep"], got["ground"], got["cost"], ref, params)
+
+
+def test_build_then_evaluate_batched_equal_single_calls():
+    """The construction-only and evaluation-only batched calls give, map by
+    map, exactly what tct_build and tct_evaluate give on each map alone."""
+    scs = _uneven_batch(seed=13, count=5)
+    maps = _maps(scs)
+    ws = torch.empty(tct.tct_workspace_bytes_batched(maps, PARAMS_ROBOT), dtype=torch.uint8,
+                     device="cuda")
+    tct.tct_build_batched(maps, ws, tct.TctTuning(tct.TILE_AUTO, 0, 2048, 0))
+    torch.cuda.synchronize()
+    for sc, m in zip(scs, maps):
+        g, c, st = P.gpu_build(sc.points, _grid(sc))
+        np.testing.assert_array_equal(m.ground.cpu().numpy(), g)
+        np.testing.assert_array_equal(m.ceil.cpu().numpy(), c)
+        mst = tct.stats_from(m.stats)
+        assert (mst.n_points, mst.n_dropped, mst.z_min, mst.z_max) == \
+               (st.n_points, st.n_dropped, st.z_min, st.z_max)
+    # the evaluation reads no plane heights: a map without points (z_min = inf) gets 0
+    z_mins = [float(np.nan_to_num(tct.stats_from(m.stats).z_min, posinf=0.0)) for m in maps]
+    ws2 = torch.empty(tct.tct_workspace_bytes_evaluate_batched(maps, PARAMS_ROBOT),
+                      dtype=torch.uint8, device="cuda")
+    tct.tct_evaluate_batched(maps, PARAMS_ROBOT, ws2)
+    torch.cuda.synchronize()
+    for sc, m, z_min in zip(scs, maps, z_mins):
+        g = m.ground.cpu().numpy()
+        grid = tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, sc.n_slices, z_min, False)
+        one = P.gpu_evaluate(g, m.ceil.cpu().numpy(), grid, PARAMS_ROBOT, aux=False)
+        np.testing.assert_array_equal(m.cost.cpu().numpy(), one["cost"])
+        np.testing.assert_array_equal(m.mask.cpu().numpy(), one["mask"])
+        np.testing.assert_array_equal(m.keep.cpu().numpy(), one["keep"])
