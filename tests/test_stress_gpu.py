@@ -33,8 +33,8 @@ import _windows as W  # noqa: E402
 import oracle  # noqa: E402
 from paper_2403_07631_gb300 import build, scenes, tct  # noqa: E402
 
-N_WINDOWS = 16
-CORE = 48
+N_WINDOWS = 64
+CORE = 64
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +60,7 @@ def _windows(sc, seed=11):
     last tile included) and some centred on cave tunnels (several layers)."""
     rng = np.random.default_rng(seed)
     out = [(0, 0), (sc.H - CORE, sc.W - CORE), (0, sc.W - CORE), (sc.H - CORE, 0)]
-    for cx, cy in sc.meta["tunnel_points"][:6]:
+    for cx, cy in sc.meta["tunnel_points"][:20]:
         i = int(cy / sc.res) - CORE // 2
         j = int(cx / sc.res) - CORE // 2
         out.append((min(max(i, 0), sc.H - CORE), min(max(j, 0), sc.W - CORE)))
