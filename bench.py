@@ -146,9 +146,10 @@ def measured_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def stack_traffic():
-    """DRAM bytes per launch of the stack kernel from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
+def stack_profile():
+    """DRAM bytes per launch and issue / ALU activity of the stack kernel from
+    the committed ncu summary; an empty dict when the kernel source changed
+    since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_stack_batched_parking.txt")
     src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cuh")
@@ -162,10 +163,12 @@ def stack_traffic():
         with open(src, "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()[:16]
         if rec.get("kernel_source_sha256_16") != digest:
-            return None
-        return int(rec["traffic_bytes_per_launch"])
+            return {}
+        return {"traffic": int(rec["traffic_bytes_per_launch"]),
+                "issue_active_pct": float(rec["issue_active_pct"]),
+                "alu_pipe_active_pct": float(rec["alu_pipe_active_pct"])}
     except (OSError, KeyError, ValueError):
-        return None
+        return {}
 
 
 def max_over_ranks(ms: float, device) -> float:
@@ -656,7 +659,7 @@ def main():
     path_gbs = algorithmic_bytes(P, N, H, W) / (ms * 1e-3) / 1e9
     sb = stack_bytes(P, N, H, W)
     stack_gbs = sb / (stack_ms * 1e-3) / 1e9
-    traffic = stack_traffic()
+    prof = stack_profile()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -668,8 +671,10 @@ def main():
                           "peak_source": peak_src},
         "roofline": {"kernel": "k_stack_batched<5,2> (per-tile incremental slice stack)", "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
-                     "traffic": traffic, "algorithmic_bytes": sb, "ms": stack_ms,
-                     "peak_source": peak_src},
+                     "traffic": prof.get("traffic"), "algorithmic_bytes": sb, "ms": stack_ms,
+                     "peak_source": peak_src,
+                     "issue_active_pct_ncu": prof.get("issue_active_pct"),
+                     "alu_pipe_active_pct_ncu": prof.get("alu_pipe_active_pct")},
         "phases_ms": {"partition": part_ms, "stack": stack_ms, "chain": chain_ms},
         "e2e": {"value": units / (e2e["ms"] * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
