@@ -146,6 +146,16 @@ def measured_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def source_digest(text: str) -> str:
+    """First 16 hex digits of the SHA-256 of a CUDA source with its // comments
+    and blank lines removed: an edit of the comments keeps the digest, any
+    change to the code changes it."""
+    import hashlib
+    import re
+    code = [re.sub(r"//.*$", "", line).rstrip() for line in text.split("\n")]
+    return hashlib.sha256("\n".join(c for c in code if c.strip()).encode()).hexdigest()[:16]
+
+
 def stack_profile():
     """DRAM bytes per launch and issue / ALU activity of the stack kernel from
     the committed ncu summary; an empty dict when the kernel source changed
@@ -160,8 +170,8 @@ def stack_profile():
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     rec[k.strip()] = v.strip()
-        with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(src) as f:
+            digest = source_digest(f.read())
         if rec.get("kernel_source_sha256_16") != digest:
             return {}
         return {"traffic": int(rec["traffic_bytes_per_launch"]),

@@ -5,16 +5,22 @@
 // radii and organised around one observation: consecutive tomogram slices
 // differ only where the plane passed a point (the redundancy Sec. III-C
 // removes afterwards).  The CTA keeps, in shared memory, the state of every
-// stage for its 64 x 64 tile and the halo and, slice after slice,
-//   1. advances each cell's pointer into its sorted z segment and marks, in
-//      per-row bit words, the cells whose ground or ceiling changed;
+// stage for its tile (64 x 64, 64 x 56 or 32 x 32 cells) and the halo and,
+// slice after slice,
+//   1. lists the cells whose next height the plane passed and advances their
+//      pointers into the sorted z segments, the list spread over all threads;
+//      per-row bit words mark the cells whose ground or ceiling changed;
 //   2. recomputes the gentle flags (Eq. 2) only in 32-column row blocks whose
-//      ground stencil changed;
-//   3. recomputes c^init (Eq. 1, 3-5) only where one of its inputs changed,
-//      marking the cells whose value changed;
+//      ground stencil changed (found one lane per block, listed, then taken
+//      by all warps in turn);
+//   3. recomputes c^init (Eq. 1, 3-5) only in the row blocks where one of its
+//      inputs changed (listed the same way), marking the cells whose value
+//      changed;
 //   4. re-inflates (Eq. 6) a warp's 32 x 8 strip only when a c^init in its
 //      window changed, otherwise keeps the previous c^T (bit-identical
-//      inputs give bit-identical results),
+//      inputs give bit-identical results), and accumulates the uniqueness
+//      bits, reading earlier costs back only for cells whose run holds a
+//      higher cost than the current one,
 // and writes all four layers of every slice.  Work follows the changes,
 // while the writes of every slice's layers (the algorithmic bytes) are
 // always done.
