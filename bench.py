@@ -160,7 +160,6 @@ def stack_profile():
     """DRAM bytes per launch and issue / ALU activity of the stack kernel from
     the committed ncu summary; an empty dict when the kernel source changed
     since the counters were taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "k_stack_batched_parking.txt")
     src = os.path.join(ROOT, "paper_2403_07631_gb300", "csrc", "tct_stack_inc.cuh")
     try:
