@@ -183,3 +183,37 @@ def test_refinement_on_tomogram_few_steps(tomogram):
     got = d_xy.cpu().numpy()
     # waypoints whose query stayed inside one lattice cell in both precisions agree tightly
     np.testing.assert_allclose(got, ref, atol=1e-4)
+
+
+def test_refinement_edges(tomogram):
+    """Zero steps and two-waypoint paths (both ends fixed) leave the paths as
+    they are; the longest path (TCT_MAX_PATH_LEN waypoints) matches the
+    oracle; too long and too short paths are refused."""
+    grid, og, cost, _ = tomogram
+    rng = np.random.default_rng(8)
+    d_c = _dev(cost)[0]
+    for paths, L, steps in ((4, 64, 0), (5, 2, 7)):
+        xy = rng.uniform(1.0, 5.0, (paths, L, 2)).astype(np.float32)
+        sl = np.zeros((paths, L), np.int32)
+        d_xy, d_sl = _dev(xy, sl)
+        tct.tct_refine_paths(grid, d_c, d_sl, d_xy, steps=steps, eta=1e-3, lam=1.0)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(d_xy.cpu().numpy(), xy)
+    L = tct.MAX_PATH_LEN
+    t = np.linspace(0.0, 1.0, L)[None, :, None]
+    xy = (np.array([1.0, 1.0]) * (1 - t) + np.array([10.0, 9.0]) * t).astype(np.float32)
+    xy[:, 1:-1] += rng.normal(0, 0.1, (1, L - 2, 2)).astype(np.float32)
+    sl = np.full((1, L), 2, np.int32)
+    d_xy, d_sl = _dev(xy, sl)
+    tct.tct_refine_paths(grid, d_c, d_sl, d_xy, steps=2, eta=1e-4, lam=1.0)
+    torch.cuda.synchronize()
+    ref = oracle.refine(og, cost, sl, xy, steps=2, eta=1e-4, lam=1.0)
+    np.testing.assert_allclose(d_xy.cpu().numpy(), ref, atol=1e-4)
+    with pytest.raises(tct.TctError, match="limit"):
+        big = torch.zeros(1, L + 1, 2, device="cuda")
+        tct.tct_refine_paths(grid, d_c, torch.zeros(1, L + 1, dtype=torch.int32, device="cuda"),
+                             big, steps=1, eta=1e-3, lam=1.0)
+    with pytest.raises(tct.TctError, match="invalid"):
+        one = torch.zeros(1, 1, 2, device="cuda")
+        tct.tct_refine_paths(grid, d_c, torch.zeros(1, 1, dtype=torch.int32, device="cuda"), one,
+                             steps=1, eta=1e-3, lam=1.0)
