@@ -303,3 +303,40 @@ def test_host_buffers_entry_point(kept_only):
         np.testing.assert_array_equal(h.numpy()[:m], ref[key][k], err_msg=key)
     if kept_only:   # beyond the kept slices the host arrays are untouched
         assert (hs[2].numpy()[m:] == -7.0).all() and (hm.numpy()[m:] == 9).all()
+
+
+def test_maximum_slice_count():
+    """N = TCT_MAX_SLICES (127): the uniqueness matrix uses all four words of
+    a row; clutter at many heights makes most slices differ."""
+    # 36 flat 10 x 10-cell patches 0.33 m apart in height, each under a slab
+    # (underside 0.6 m, top 0.7 m above its floor): every floor is the ground
+    # of a few slices only, so slices up to ~123 are kept
+    rng = np.random.default_rng(31)
+    jj, ii = np.meshgrid(np.arange(60), np.arange(60))
+    jj, ii = np.repeat(jj.ravel(), 3), np.repeat(ii.ravel(), 3)
+    z = 0.33 * ((ii // 10) * 6 + jj // 10) + np.tile([0.0, 0.6, 0.7], 3600)
+    z = z + rng.normal(0, 0.003, ii.size)
+    pts = np.stack([(jj + rng.random(jj.size)) * 0.1, (ii + rng.random(ii.size)) * 0.1, z],
+                   1).astype(np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 60, 60, 0.1, tct.MAX_SLICES, 0.0, True)
+    params = dict(PARAMS_ROBOT, d_min=0.1, d_ref=0.2, flags=tct.ALLOW_COARSE)
+    g, _ = _full_check(pts, grid, params)
+    kept = np.flatnonzero(g["keep"])
+    assert len(kept) > 20 and kept[-2] > 96      # the fourth word of a uniqueness row in use
+    with pytest.raises(tct.TctError):
+        bad = tct.Grid(0.0, 0.0, 0.1, 60, 60, 0.1, tct.MAX_SLICES + 1, 0.0, True)
+        P.gpu_build_evaluate(pts, bad, params)
+
+
+def test_maximum_window_and_patch_radius():
+    """Inflation radius 15 cells (d_inf 0.4 m, d_sm 0.45 m at 0.05 m) and p_s
+    patch radius 4, the largest the ABI takes (the generic kernel); one more
+    cell of either is refused."""
+    sc = scenes.building(32, 50_000, side_cells=90, res=0.05, floors=[0.0, 1.2],
+                         ceilings=[1.0, 2.6])
+    params = dict(PARAMS_ROBOT, d_inf=0.4, d_sm=0.45, patch_radius=4)
+    _full_check(sc.points, _grid_of(sc, n_slices=6), params)
+    with pytest.raises(tct.TctError, match="limit"):
+        P.gpu_build_evaluate(sc.points, _grid_of(sc, n_slices=6), dict(params, d_sm=0.5))
+    with pytest.raises(tct.TctError):
+        P.gpu_build_evaluate(sc.points, _grid_of(sc, n_slices=6), dict(params, patch_radius=5))
