@@ -1,8 +1,10 @@
 """Pins of the oracle's cost/elevation queries (the C(q), e^G(q) of Eq. 10):
 bilinear reproduction of linear fields with their constant gradient, a
 2x2 example worked by hand, clamping at the border, the invalid-ground fill,
-the analytic gradient against central differences, and the refinement
-objective's descent property."""
+the analytic gradient against central differences, and the refinement:
+its descent property, a straight equally spaced path as a fixed point of
+the smoothness term, one step on a linear cost moving each interior
+waypoint by exactly -eta * gradient, and translation invariance."""
 import numpy as np
 import pytest
 
@@ -92,3 +94,47 @@ def test_refinement_descends_smooth_bowl(oracle_mod):
     out = oracle_mod.refine(g, cost, np.zeros((1, L)), xy, steps=200, eta=1e-2, lam=1.0)
     assert np.all(np.abs(out[0, 1:-1, 1] - 2.0) < np.abs(xy[0, 1:-1, 1] - 2.0))
     np.testing.assert_array_equal(out[0, [0, -1]], xy[0, [0, -1]])
+
+
+def test_refinement_straight_path_is_a_fixed_point(oracle_mod):
+    # zero cost: only the smoothness term acts, and an equally spaced straight
+    # path has every second difference zero
+    H = W = 30
+    g = _grid(oracle_mod, H, W)
+    cost = np.zeros((1, H, W), np.float32)
+    L = 25
+    t = np.linspace(0.0, 1.0, L)[:, None]
+    xy = (np.array([0.4, 0.7]) * (1 - t) + np.array([2.6, 2.1]) * t)[None]
+    out = oracle_mod.refine(g, cost, np.zeros((1, L)), xy, steps=40, eta=1e-2, lam=1.0)
+    np.testing.assert_allclose(out, xy, atol=1e-12)
+
+
+def test_refinement_linear_cost_moves_by_eta_times_gradient(oracle_mod):
+    # lambda = 0 and a linear cost field (reproduced exactly by the bilinear
+    # query, with a constant gradient): one step moves every interior
+    # waypoint by exactly -eta * gradient, the ends stay
+    H, W = 30, 40
+    a, b = 0.8, -0.5
+    jj, ii = np.meshgrid(np.arange(W), np.arange(H))
+    cost = (10.0 + a * (jj + 0.5) * 0.1 + b * (ii + 0.5) * 0.1).astype(np.float32)[None]
+    g = _grid(oracle_mod, H, W)
+    rng = np.random.default_rng(3)
+    xy = np.stack([rng.uniform(0.5, 3.5, 12), rng.uniform(0.5, 2.5, 12)], 1)[None]
+    eta = 1e-2
+    out = oracle_mod.refine(g, cost, np.zeros((1, 12)), xy, steps=1, eta=eta, lam=0.0)
+    expect = xy.astype(np.float32).astype(np.float64).copy()
+    expect[0, 1:-1] -= eta * np.array([a, b])
+    np.testing.assert_allclose(out[0, 1:-1], expect[0, 1:-1], rtol=0, atol=1e-6)
+    np.testing.assert_array_equal(out[0, [0, -1]], xy[0, [0, -1]])
+
+
+def test_refinement_is_translation_invariant_without_cost(oracle_mod):
+    H = W = 40
+    g = _grid(oracle_mod, H, W)
+    cost = np.zeros((1, H, W), np.float32)
+    rng = np.random.default_rng(4)
+    xy = np.stack([np.linspace(0.5, 2.5, 20), 1.0 + rng.normal(0, 0.1, 20)], 1)[None]
+    shift = np.array([0.75, 1.25])
+    a = oracle_mod.refine(g, cost, np.zeros((1, 20)), xy, steps=5, eta=1e-2, lam=1.0)
+    b = oracle_mod.refine(g, cost, np.zeros((1, 20)), xy + shift, steps=5, eta=1e-2, lam=1.0)
+    np.testing.assert_allclose(b - shift, a, atol=1e-9)
