@@ -179,3 +179,18 @@ def test_nonfinite_points_are_rejected(oracle_mod):
     eG, eC, _, dropped, bad = oracle_mod.build(pts, g, zmin_from_data=False)
     assert bad == 3 and dropped == 0
     assert eG[0, 0, 0] == 0.0 and np.all(eC == np.inf)
+
+
+def test_bounds_against_numpy(oracle_mod):
+    """The cloud bounds are numpy's min / max over the finite points, with the
+    non-finite ones counted (and -0 read as +0, which compares equal)."""
+    rng = np.random.default_rng(12)
+    pts = rng.normal(0, 5, (5000, 3)).astype(np.float32)
+    pts[::97, 1] = np.nan
+    pts[3::101, 2] = np.inf
+    pts[5::89, 0] = -np.inf
+    b, bad = oracle_mod.bounds(pts)
+    ok = np.isfinite(pts).all(1)
+    assert bad == int((~ok).sum())
+    np.testing.assert_array_equal(b[:3], pts[ok].min(0).astype(np.float64))
+    np.testing.assert_array_equal(b[3:], pts[ok].max(0).astype(np.float64))
