@@ -340,3 +340,31 @@ def test_maximum_window_and_patch_radius():
         P.gpu_build_evaluate(sc.points, _grid_of(sc, n_slices=6), dict(params, d_sm=0.5))
     with pytest.raises(tct.TctError):
         P.gpu_build_evaluate(sc.points, _grid_of(sc, n_slices=6), dict(params, patch_radius=5))
+
+
+@pytest.mark.parametrize("stride", [3, 4])
+def test_bounds_and_planned_grid(stride):
+    """tct_bounds against the oracle's bounds (finite points only, the others
+    counted), and the grid tct_plan_grid derives from them against the
+    oracle's (Sec. III-A: footprint, z_min, plane count)."""
+    sc = scenes.two_storey_building()
+    pts = sc.points.copy()
+    pts[::501, 0] = np.nan
+    pts[7::613, 2] = np.inf
+    d = torch.from_numpy(pts)
+    if stride == 4:
+        d = torch.cat([d, torch.zeros(len(d), 1)], 1).contiguous()
+    d = d.cuda()
+    out6 = torch.empty(6, device="cuda")
+    stats = torch.zeros(tct.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    tct.tct_bounds(d, out6, stats)
+    torch.cuda.synchronize()
+    ref, bad = P.oracle.bounds(pts)
+    got = out6.cpu().numpy()
+    np.testing.assert_array_equal(got.astype(np.float64), ref)
+    st = tct.stats_from(stats)
+    assert st.n_nonfinite == bad > 0 and st.status & tct.DEV_NONFINITE
+    g = tct.tct_plan_grid(got, 0.1, 0.5)
+    og = P.oracle.derive_grid(pts, 0.1, 0.5)
+    assert (g.W, g.H, g.n_slices) == (og.W, og.H, og.N)
+    assert (g.x0, g.y0, g.z_min) == (og.x0, og.y0, og.z_min)
