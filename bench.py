@@ -703,20 +703,24 @@ def main():
         "valid_frac_per_slice": [round(st.valid_cells[k] / (H * W), 4) for k in range(N)],
         "trav_frac_per_slice": [round(st.trav_cells[k] / (H * W), 4) for k in range(N)],
     }
-    out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
-    out["small_map"] = small_map_graph(dev, params, args.steps)
-    if not args.no_planner:
-        out["planned_paths"] = planned_paths(dev, grid, params, ground, cost, keep, stats)
-    if not args.no_batched:
-        del ws, ground, ceil, cost, mask, keep
-        torch.cuda.empty_cache()
-        out["batched_vs_plain"] = batched_vs_plain(dev, params, min(args.steps, 5))
-        torch.cuda.empty_cache()
-    if not args.no_stress:
-        if args.no_batched:
+    # the single-GPU measurements beside the headline (queries, small-map graph,
+    # path search, batches, stress) run at N = 1 only; at N > 1 every rank
+    # would repeat them on shared host cores
+    if world == 1:
+        out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
+        out["small_map"] = small_map_graph(dev, params, args.steps)
+        if not args.no_planner:
+            out["planned_paths"] = planned_paths(dev, grid, params, ground, cost, keep, stats)
+        if not args.no_batched:
             del ws, ground, ceil, cost, mask, keep
             torch.cuda.empty_cache()
-        out["stress"] = stress(dev, params, min(args.steps, 3))
+            out["batched_vs_plain"] = batched_vs_plain(dev, params, min(args.steps, 5))
+            torch.cuda.empty_cache()
+        if not args.no_stress:
+            if args.no_batched:
+                del ws, ground, ceil, cost, mask, keep
+                torch.cuda.empty_cache()
+            out["stress"] = stress(dev, params, min(args.steps, 3))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, params)
     if world > 1:
