@@ -114,3 +114,32 @@ def test_argument_errors_need_no_gpu(lib):
     rc = lib.tct_evaluate(ctypes.byref(g), ctypes.byref(P), fake, fake, fake, 1 << 30,
                           fake, fake, fake, None, None, None)
     assert rc == -4
+
+
+def test_constants_match_the_header(tmp_path):
+    """Every constant the binding mirrors has the header's value."""
+    import shutil
+    import subprocess
+    from paper_2403_07631_gb300 import tct
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"TCT_OK": tct.OK, "TCT_MAX_SLICES": tct.MAX_SLICES,
+             "TCT_GRID_ZMIN_FROM_DATA": tct.GRID_ZMIN_FROM_DATA, "TCT_KEEP_ENDS": tct.KEEP_ENDS,
+             "TCT_ALLOW_COARSE": tct.ALLOW_COARSE, "TCT_DEV_NONFINITE": tct.DEV_NONFINITE,
+             "TCT_DEV_BAD_QUERY": tct.DEV_BAD_QUERY, "TCT_MAX_PATH_LEN": tct.MAX_PATH_LEN,
+             "TCT_NOALLOC_SCRATCH_BYTES": tct.NOALLOC_SCRATCH_BYTES,
+             "TCT_MAX_BATCH": tct.MAX_BATCH, "TCT_TILE_AUTO": tct.TILE_AUTO,
+             "TCT_TILE_64": tct.TILE_64, "TCT_TILE_32": tct.TILE_32,
+             "TCT_TILE_64x56": tct.TILE_64x56, "TCT_HOST_KEPT_ONLY": tct.HOST_KEPT_ONLY}
+    lines = ['#include <stdio.h>', '#include "tct.h"', 'int main(void) {']
+    lines += [f'    printf("{k} %lld\\\\n", (long long)({k}));' for k in pairs]
+    lines += ['    return 0;', '}']
+    src = tmp_path / "consts.c"
+    src.write_text("\\n".join(lines) + "\\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in filter(None, out.split("\\n")):
+        name, value = line.split()
+        assert pairs[name] == int(value), f"{name}: binding {pairs[name]}, header {value}"
