@@ -133,13 +133,13 @@ def test_constants_match_the_header(tmp_path):
              "TCT_TILE_64": tct.TILE_64, "TCT_TILE_32": tct.TILE_32,
              "TCT_TILE_64x56": tct.TILE_64x56, "TCT_HOST_KEPT_ONLY": tct.HOST_KEPT_ONLY}
     lines = ['#include <stdio.h>', '#include "tct.h"', 'int main(void) {']
-    lines += [f'    printf("{k} %lld\\\\n", (long long)({k}));' for k in pairs]
+    lines += [f'    printf("{k} %lld\\n", (long long)({k}));' for k in pairs]
     lines += ['    return 0;', '}']
     src = tmp_path / "consts.c"
-    src.write_text("\\n".join(lines) + "\\n")
+    src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "consts"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
-    for line in filter(None, out.split("\\n")):
+    for line in filter(None, out.split("\n")):
         name, value = line.split()
         assert pairs[name] == int(value), f"{name}: binding {pairs[name]}, header {value}"
