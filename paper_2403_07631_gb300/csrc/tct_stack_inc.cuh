@@ -55,6 +55,7 @@ struct Geo {
     static constexpr int GPASS = (GW + 31) / 32, CPASS = (CW + 31) / 32;
     static constexpr int WORDS = 4 * EH * EWW + 2 * GH * GWW + CH * CWW;
     static_assert(NE < 65536, "16-bit indices of the elevation region");
+    static_assert(NE % 4 == 0, "the elevation region is read four cells at a time");
     static constexpr size_t smem_bytes() {
         // state, change words, 16-bit pointer offsets, 16-bit list of the
         // cells a plane passed
@@ -129,6 +130,13 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     const int64_t HW = (int64_t)a.W * a.H;
     const float ts2 = c.theta_s * c.theta_s;   // m^grad < theta_s  <=>  m^2 < theta_s^2
     const float inv_ts2 = c.inv_ts * c.inv_ts;
+    // the columns a 32-wide block or strip reads, as masks of its own change
+    // word (Lo) and of the next one (Hi)
+    static_assert(RP + 2 < 32 && 2 * RP < 32 && 2 * RK < 32, "windows span two change words");
+    constexpr uint32_t kGrndLo = ~0u << RP, kGrndHi = (1u << (RP + 2)) - 1u;
+    constexpr uint32_t kCeilLo = ~0u << (RP + 1), kCeilHi = (1u << (RP + 1)) - 1u;
+    constexpr uint32_t kGentHi = (1u << (2 * RP)) - 1u;
+    constexpr uint32_t kWinHi = (1u << (2 * RK)) - 1u;
 
     if (tid < 2) counters.nlist[tid] = 0;
     for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
@@ -249,19 +257,28 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         uint32_t *sChgC = sChgC0 + (k & 1) * G::EH * G::EWW;
 
         // ---- 1. grounds and ceilings: advance the pointers past h ----
-        // 1a. list the cells whose next height the plane passed (one shared
-        //     counter add per warp)
+        // 1a. list the cells whose next height the plane passed: four cells a
+        //     thread (one 16-byte load), one shared counter add per warp
         int32_t *nlist = &counters.nlist[k & 1];
         if (tid == 0) counters.nwork[0] = counters.nwork[1] = 0;   // read before the last barrier
-        for (int base = 0; base < G::NE; base += kNT) {
-            const int e = base + tid;
-            const bool pass = e < G::NE && sZC[e] <= h;
-            const uint32_t m = __ballot_sync(0xffffffffu, pass);
-            if (m) {
+        for (int base = 0; base < G::NE / 4; base += kNT) {
+            const int e4 = base + tid;
+            float4 z = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            if (e4 < G::NE / 4) z = reinterpret_cast<const float4 *>(sZC)[e4];
+            const bool p0 = z.x <= h, p1 = z.y <= h, p2 = z.z <= h, p3 = z.w <= h;
+            if (__any_sync(0xffffffffu, p0 || p1 || p2 || p3)) {
+                const uint32_t m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
+                const uint32_t m2 = __ballot_sync(0xffffffffu, p2), m3 = __ballot_sync(0xffffffffu, p3);
+                const uint32_t lt = (1u << lane) - 1u;
+                const int n0 = __popc(m0), n01 = n0 + __popc(m1), n012 = n01 + __popc(m2);
                 int at = 0;
-                if (lane == 0) at = atomicAdd(nlist, __popc(m));
+                if (lane == 0) at = atomicAdd(nlist, n012 + __popc(m3));
                 at = __shfl_sync(0xffffffffu, at, 0);
-                if (pass) sList[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
+                const int e = 4 * e4;
+                if (p0) sList[at + __popc(m0 & lt)] = (uint16_t)e;
+                if (p1) sList[at + n0 + __popc(m1 & lt)] = (uint16_t)(e + 1);
+                if (p2) sList[at + n01 + __popc(m2 & lt)] = (uint16_t)(e + 2);
+                if (p3) sList[at + n012 + __popc(m3 & lt)] = (uint16_t)(e + 3);
             }
         }
         __syncthreads();
@@ -320,7 +337,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
                 uint32_t v = 0;
 #pragma unroll
                 for (int dr = 0; dr < 3; ++dr)
-                    v |= sChgG[(gr + dr) * G::EWW + w] | sChgG[(gr + dr) * G::EWW + w + 1];
+                    v |= sChgG[(gr + dr) * G::EWW + w] | (sChgG[(gr + dr) * G::EWW + w + 1] & 3u);
                 dirty = first || v != 0;
                 if (!dirty) sGChg[gr * G::GWW + w] = 0;
             }
@@ -387,13 +404,17 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             bool dirty = false;
             if (blk < G::CH * G::CPASS) {
                 const int cr = blk / G::CPASS, w = blk - cr * G::CPASS;
-                uint32_t v = sChgC[(cr + RP + 1) * G::EWW + w] | sChgC[(cr + RP + 1) * G::EWW + w + 1];
+                // exact column ranges: ground columns 32w+RP .. 32w+RP+33, the
+                // ceiling's 32w+RP+1 .. 32w+RP+32, gentle flags 32w .. 32w+31+2RP
+                uint32_t v = (sChgC[(cr + RP + 1) * G::EWW + w] & kCeilLo) |
+                             (sChgC[(cr + RP + 1) * G::EWW + w + 1] & kCeilHi);
 #pragma unroll
                 for (int dr = 0; dr < 3; ++dr)
-                    v |= sChgG[(cr + RP + dr) * G::EWW + w] | sChgG[(cr + RP + dr) * G::EWW + w + 1];
+                    v |= (sChgG[(cr + RP + dr) * G::EWW + w] & kGrndLo) |
+                         (sChgG[(cr + RP + dr) * G::EWW + w + 1] & kGrndHi);
 #pragma unroll
                 for (int dr = 0; dr <= 2 * RP; ++dr)
-                    v |= sGChg[(cr + dr) * G::GWW + w] | sGChg[(cr + dr) * G::GWW + w + 1];
+                    v |= sGChg[(cr + dr) * G::GWW + w] | (sGChg[(cr + dr) * G::GWW + w + 1] & kGentHi);
                 dirty = first || v != 0;
                 if (!dirty) sCIChg[cr * G::CWW + w] = 0;
             }
@@ -467,7 +488,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         // ---- 4. inflation (Eq. 6) of the strip, uniqueness, outputs ----
         uint32_t v = 0;
         for (int x = lane; x < 2 * (kStrip + 2 * RK); x += 32)
-            v |= sCIChg[(tr0 + (x >> 1)) * G::CWW + half + (x & 1)];
+            v |= sCIChg[(tr0 + (x >> 1)) * G::CWW + half + (x & 1)] & ((x & 1) ? kWinHi : ~0u);
         const bool need_infl = __any_sync(0xffffffffu, v != 0);
         const bool need_simp = need_infl || __any_sync(0xffffffffu, gchbits != 0);
         if (need_simp) {
