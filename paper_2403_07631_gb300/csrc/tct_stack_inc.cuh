@@ -376,18 +376,12 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         }
         __syncthreads();
 
-        // ---- the strip's ground and ceiling outputs and own changes ----
+        // ---- the strip's own ground changes ----
         uint32_t gchbits = 0;
 #pragma unroll
         for (int q = 0; q < kStrip; ++q) {
             const int er = tr0 + q + G::HE, es = ts + G::HE;
-            const int i = ty0 + tr0 + q;
             const float eg = sEG[er * G::EW + es];
-            if (i < a.H && j_out < a.W) {
-                const int64_t o = (int64_t)k * HW + (int64_t)i * a.W + j_out;
-                __stcs(&a.ground[o], eg);
-                __stcs(&a.ceil[o], sZC[er * G::EW + es]);
-            }
             if (first || ((sChgG[er * G::EWW + (es >> 5)] >> (es & 31)) & 1u)) {
                 gchbits |= 1u << q;
                 if (eg > -INFINITY) validbits |= 1u << q;
@@ -580,7 +574,12 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             for (int q = 0; q < kStrip; ++q) {
                 const int i = ty0 + tr0 + q;
                 if (i < a.H) {
+                    // ground and ceiling are still this slice's: the next
+                    // slice advances them after its first barrier
+                    const int e = (tr0 + q + G::HE) * G::EW + ts + G::HE;
                     const int64_t o = (int64_t)k * HW + (int64_t)i * a.W + j_out;
+                    __stcs(&a.ground[o], sEG[e]);
+                    __stcs(&a.ceil[o], sZC[e]);
                     __stcs(&a.cost[o], cT[q]);
                     a.mask[o] = (travbits >> q) & 1u;
                 }
