@@ -145,18 +145,35 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         s_trav[i] = 0;
     }
     for (int i = tid; i < G::WORDS; i += kNT) sChgG0[i] = 0;
-    for (int e = tid; e < G::NE; e += kNT) {
-        const int r = e / G::EW, s = e - r * G::EW;
-        const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
-        float zc = INFINITY;
-        if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
-            const int64_t cell = (int64_t)i * a.W + j;
-            const int32_t p = a.start[cell];
-            if (p < a.start[cell + 1]) zc = a.zs[p];
+    // each cell's lowest height; four cells a thread at a time, so that their
+    // segment and height loads are in flight together
+    constexpr int kInit = 4;
+    for (int e0 = tid; e0 < G::NE; e0 += kInit * kNT) {
+        int32_t b[kInit], end[kInit];
+#pragma unroll
+        for (int u = 0; u < kInit; ++u) {
+            const int e = e0 + u * kNT;
+            const int r = e / G::EW, s = e - r * G::EW;
+            const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
+            b[u] = end[u] = 0;
+            if (e < G::NE && i >= 0 && i < a.H && j >= 0 && j < a.W) {
+                const int64_t cell = (int64_t)i * a.W + j;
+                b[u] = a.start[cell];
+                end[u] = a.start[cell + 1];
+            }
         }
-        sEG[e] = -INFINITY;
-        sZC[e] = zc;
-        sOff[e] = 0;
+        float zc[kInit];
+#pragma unroll
+        for (int u = 0; u < kInit; ++u) zc[u] = b[u] < end[u] ? a.zs[b[u]] : INFINITY;
+#pragma unroll
+        for (int u = 0; u < kInit; ++u) {
+            const int e = e0 + u * kNT;
+            if (e < G::NE) {
+                sEG[e] = -INFINITY;
+                sZC[e] = zc[u];
+                sOff[e] = 0;
+            }
+        }
     }
     float z_min = a.z_min;
     if (a.zmin_from_data) {
