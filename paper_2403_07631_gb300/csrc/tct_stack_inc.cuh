@@ -190,6 +190,10 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     uint32_t run_lo = 0, run_hi = 0;           // run starts, one byte per cell
     uint32_t validbits = 0, travbits = 0;
     int wvalid = 0, wtrav = 0;
+    // the strip's cells inside the map, one bit per row
+    const int rows_in = a.H - (ty0 + tr0);
+    const uint32_t inmap = j_out >= a.W || rows_in <= 0 ? 0u
+                           : (rows_in >= kStrip ? (1u << kStrip) - 1u : (1u << rows_in) - 1u);
 #pragma unroll
     for (int q = 0; q < kStrip; ++q) cT[q] = 0.0f;
     auto run_get = [&](int q) -> int {
@@ -541,9 +545,8 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             uint32_t walk = 0;
 #pragma unroll
             for (int q = 0; q < kStrip; ++q) {
-                const int i = ty0 + tr0 + q;
                 const bool gq = (gchbits >> q) & 1u;
-                if (!first && i < a.H && j_out < a.W && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
+                if (!first && ((inmap >> q) & 1u) && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
                     if (!((runle >> q) & 1u)) walk |= 1u << q;
                     pre = max(pre, run_get(q) + 1);
                 }
@@ -572,15 +575,8 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
 #pragma unroll
             for (int q = 0; q < kStrip; ++q)
                 if (cT[q] < c.c_b) travbits |= 1u << q;
-            int nv = 0, nt = 0;
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const bool in_map = ty0 + tr0 + q < a.H && j_out < a.W;
-                nv += __popc(__ballot_sync(0xffffffffu, in_map && ((validbits >> q) & 1u)));
-                nt += __popc(__ballot_sync(0xffffffffu, in_map && ((travbits >> q) & 1u)));
-            }
-            wvalid = nv;
-            wtrav = nt;
+            wvalid = (int)__reduce_add_sync(0xffffffffu, (uint32_t)__popc(validbits & inmap));
+            wtrav = (int)__reduce_add_sync(0xffffffffu, (uint32_t)__popc(travbits & inmap));
         }
         if (lane == 0) {
             if (wvalid) atomicAdd(&s_valid[k], wvalid);
@@ -610,8 +606,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         uint32_t walk = 0;
 #pragma unroll
         for (int q = 0; q < kStrip; ++q) {
-            const int i = ty0 + tr0 + q;
-            if (i < a.H && j_out < a.W && cT[q] < c.c_b) {
+            if (((inmap >> q) & 1u) && cT[q] < c.c_b) {
                 if (!((runle >> q) & 1u)) walk |= 1u << q;
                 pre = max(pre, run_get(q) + 1);
             }
