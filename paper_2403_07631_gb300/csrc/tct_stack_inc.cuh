@@ -199,10 +199,10 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     auto run_get = [&](int q) -> int {
         return q < 4 ? (run_lo >> (8 * q)) & 0xffu : (run_hi >> (8 * (q - 4))) & 0xffu;
     };
-    // per cell, an upper bound of c^T over its run before the current slice:
-    // fp16 rounded up (never below the true maximum), -inf for an empty run;
-    // with the exact flag below it decides whether a cell can set a bit of
-    // U(p, k-1) for p in its run; cells that cannot skip the walk
+    // per cell, an upper bound of c^T over its run before the current slice,
+    // fp16 rounded up (never below the true maximum), kept while the flag
+    // below is clear; with the flag it decides whether a cell can set a bit
+    // of U(p, k-1) for p in its run; cells that cannot skip the walk
     uint32_t rmax[kStrip / 2];
 #pragma unroll
     for (int q = 0; q < kStrip / 2; ++q) rmax[q] = 0xfc00fc00u;
@@ -554,18 +554,27 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             if (!first) mark_run(walk, k - 1);
 #pragma unroll
             for (int q = 0; q < kStrip; ++q) {
-                if ((gchbits >> q) & 1u) {
+                const uint32_t bit = 1u << q;
+                if (gchbits & bit) {
                     run_set(q, k);
-                    rmax_set(q, 0xfc00u);
-                    runle |= 1u << q;
+                    runle |= bit;
                 } else if (!first) {
-                    // the run now covers slice k-1 (cost cT) and the current cost is acc:
-                    // max(run, cT) <= acc  <=  cT <= acc and (old flag or bound <= acc)
-                    const float mup = rmax_get(q);
-                    const bool le = cT[q] <= acc[q] && (((runle >> q) & 1u) || mup <= acc[q]);
-                    runle = le ? runle | (1u << q) : runle & ~(1u << q);
-                    const __half hc = __float2half_ru(cT[q]);
-                    if (__half2float(hc) > mup) rmax_set(q, __half_as_ushort(hc));
+                    // the run now covers slice k-1 (cost cT) and the current cost is acc
+                    if (runle & bit) {
+                        // no earlier cost of the run exceeded cT, so the run's
+                        // maximum is cT: the flag stays while cT <= acc, and the
+                        // bound (unused while the flag holds) starts at cT
+                        if (!(cT[q] <= acc[q])) {
+                            runle &= ~bit;
+                            rmax_set(q, __half_as_ushort(__float2half_ru(cT[q])));
+                        }
+                    } else {
+                        // max(run, cT) <= acc  <=  cT <= acc and bound <= acc
+                        const float mup = rmax_get(q);
+                        if (cT[q] <= acc[q] && mup <= acc[q]) runle |= bit;
+                        const __half hc = __float2half_ru(cT[q]);
+                        if (__half2float(hc) > mup) rmax_set(q, __half_as_ushort(hc));
+                    }
                 }
                 cT[q] = acc[q];
             }
