@@ -68,6 +68,7 @@ struct Geo {
 struct SliceCounters {
     int32_t nlist[2];                  // cells a plane passed, slices of even / odd k
     int32_t nwork[2];                  // dirty row blocks: gentle flags, c^init
+    uint32_t infl;                     // warps whose strip is re-inflated this slice
     int32_t upre[TCT_MAX_SLICES + 1];
     int32_t valid[TCT_MAX_SLICES + 1];
     int32_t trav[TCT_MAX_SLICES + 1];
@@ -88,6 +89,44 @@ __device__ __forceinline__ int32_t upper_bound(const float *__restrict__ zs, int
         else e = m;
     }
     return s;
+}
+
+// Eq. 6 for NQ cells of one column: acc[q] = max over the window of K * c^init
+// for the cell of row q, where row0 points at the cell's column (less R_K) in
+// the first of the NQ + 2 R_K c^init rows it reads, CW floats apart.  Every
+// c^init row is loaded once, folded into pair maxima max(c(j-d), c(j+d)),
+// weighted and reduced with the three-input max.
+template <int RK, int NQ, int CW>
+__device__ __forceinline__ void inflate_column(const float *row0, const EvalConsts &c,
+                                               float (&acc)[NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
+    // wide windows (R_K > 8) keep the row loop rolled: the full unrolling of
+    // a 25 x 25 window costs minutes of compilation
+#pragma unroll(RK <= 8 ? NQ + 2 * RK : 1)
+    for (int rr = 0; rr < NQ + 2 * RK; ++rr) {
+        const float *row = row0 + rr * CW;
+        float P[RK + 1];
+        P[0] = row[RK];
+#pragma unroll
+        for (int d = 1; d <= RK; ++d) P[d] = fmaxf(row[RK - d], row[RK + d]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int n = rr - RK - q;       // row offset of this row for cell q
+            if (n < -RK || n > RK) continue;
+            const int an = n < 0 ? -n : n;
+            const float *Kr = c.K + (an + RK) * (2 * RK + 1) + RK;
+            // the disc d^2 < (RK+1)^2 holds every positive weight
+#pragma unroll
+            for (int d = 0; d <= RK; d += 2) {
+                if (d * d + an * an >= (RK + 1) * (RK + 1)) break;
+                const float t0 = Kr[d] * P[d];
+                const float t1 = (d + 1 <= RK && (d + 1) * (d + 1) + an * an < (RK + 1) * (RK + 1))
+                                     ? Kr[d + 1] * P[d + 1] : 0.0f;
+                acc[q] = max3(acc[q], t0, t1);
+            }
+        }
+    }
 }
 
 // The per-map fields the incremental slice stack reads and writes.
@@ -139,6 +178,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     constexpr uint32_t kWinHi = (1u << (2 * RK)) - 1u;
 
     if (tid < 2) counters.nlist[tid] = 0;
+    if (tid == 0) counters.infl = 0;
     for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
         s_upre[i] = 0;
         s_valid[i] = 0;
@@ -303,6 +343,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             }
         }
         __syncthreads();
+        if (tid == 0) counters.infl = 0;   // last read before this barrier
         // 1b. advance the listed cells, spread evenly over the threads; each
         //     round reads the next four heights of the segment at once, so a
         //     cell that passes n heights waits for ceil(n / 4) loads, not n
@@ -505,41 +546,40 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         for (int x = lane; x < 2 * (kStrip + 2 * RK); x += 32)
             v |= sCIChg[(tr0 + (x >> 1)) * G::CWW + half + (x & 1)] & ((x & 1) ? kWinHi : ~0u);
         const bool need_infl = __any_sync(0xffffffffu, v != 0);
+        if (lane == 0 && need_infl) atomicOr(&counters.infl, 1u << warp);
+        __syncthreads();
+        const uint32_t dmask = counters.infl;
+        const int ndirty = __popc(dmask);
+        float acc[kStrip];
+#pragma unroll
+        for (int q = 0; q < kStrip; ++q) acc[q] = cT[q];
+        if (ndirty > 0 && 2 * ndirty <= kNW) {
+            // few strips changed: their halves (kStrip / 2 rows each) are
+            // spread over the warps, half j on warp j, and handed to the
+            // owner through the block list (free until the next slice)
+            float *slots = reinterpret_cast<float *>(sList);
+            if (warp < 2 * ndirty) {
+                uint32_t m = dmask;
+                for (int r = warp >> 1; r > 0; --r) m &= m - 1u;
+                const int owner = __ffs(m) - 1;
+                const int o_tr0 = kStrip * (owner / G::NHALF) + (warp & 1) * (kStrip / 2);
+                const int o_ts = 32 * (owner % G::NHALF) + lane;
+                float a2[kStrip / 2];
+                inflate_column<RK, kStrip / 2, G::CW>(sCI + o_tr0 * G::CW + o_ts, c, a2);
+#pragma unroll
+                for (int u = 0; u < kStrip / 2; ++u) slots[(warp * (kStrip / 2) + u) * 32 + lane] = a2[u];
+            }
+            __syncthreads();
+            if (need_infl) {
+                const int rank = __popc(dmask & ((1u << warp) - 1u));
+#pragma unroll
+                for (int q = 0; q < kStrip; ++q) acc[q] = slots[(2 * rank * (kStrip / 2) + q) * 32 + lane];
+            }
+        } else if (need_infl) {
+            inflate_column<RK, kStrip, G::CW>(sCI + tr0 * G::CW + ts, c, acc);
+        }
         const bool need_simp = need_infl || __any_sync(0xffffffffu, gchbits != 0);
         if (need_simp) {
-            float acc[kStrip];
-#pragma unroll
-            for (int q = 0; q < kStrip; ++q) acc[q] = cT[q];
-            if (need_infl) {
-#pragma unroll
-                for (int q = 0; q < kStrip; ++q) acc[q] = 0.0f;
-                // wide windows (R_K > 8) keep the row loop rolled: the full
-                // unrolling of a 25 x 25 window costs minutes of compilation
-#pragma unroll(RK <= 8 ? kStrip + 2 * RK : 1)
-                for (int rr = 0; rr < kStrip + 2 * RK; ++rr) {
-                    const float *row = sCI + (tr0 + rr) * G::CW + ts;
-                    float P[RK + 1];
-                    P[0] = row[RK];
-#pragma unroll
-                    for (int d = 1; d <= RK; ++d) P[d] = fmaxf(row[RK - d], row[RK + d]);
-#pragma unroll
-                    for (int q = 0; q < kStrip; ++q) {
-                        const int n = rr - RK - q;       // row offset of this row for cell q
-                        if (n < -RK || n > RK) continue;
-                        const int an = n < 0 ? -n : n;
-                        const float *Kr = c.K + (an + RK) * (2 * RK + 1) + RK;
-                        // the disc d^2 < (RK+1)^2 holds every positive weight
-#pragma unroll
-                        for (int d = 0; d <= RK; d += 2) {
-                            if (d * d + an * an >= (RK + 1) * (RK + 1)) break;
-                            const float t0 = Kr[d] * P[d];
-                            const float t1 = (d + 1 <= RK && (d + 1) * (d + 1) + an * an < (RK + 1) * (RK + 1))
-                                                 ? Kr[d + 1] * P[d + 1] : 0.0f;
-                            acc[q] = max3(acc[q], t0, t1);
-                        }
-                    }
-                }
-            }
             // Eq. 9 of slice k-1 against slice k, then the rows p it is unique against
             int pre = 0;
             uint32_t walk = 0;
