@@ -631,19 +631,22 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             if (wvalid) atomicAdd(&s_valid[k], wvalid);
             if (wtrav) atomicAdd(&s_trav[k], wtrav);
         }
-        if (j_out < a.W) {
+        if (inmap) {
+            // this slice's layers, addressed by 32-bit offsets within the
+            // slice (W H <= 2^30); ground and ceiling are still this slice's:
+            // the next slice advances them after its first barrier
+            const int64_t sl = (int64_t)k * HW;
+            float *gk = a.ground + sl, *zk = a.ceil + sl, *tk = a.cost + sl;
+            uint8_t *mk = a.mask + sl;
+            uint32_t o = (uint32_t)(ty0 + tr0) * (uint32_t)a.W + (uint32_t)j_out;
 #pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const int i = ty0 + tr0 + q;
-                if (i < a.H) {
-                    // ground and ceiling are still this slice's: the next
-                    // slice advances them after its first barrier
+            for (int q = 0; q < kStrip; ++q, o += (uint32_t)a.W) {
+                if ((inmap >> q) & 1u) {
                     const int e = (tr0 + q + G::HE) * G::EW + ts + G::HE;
-                    const int64_t o = (int64_t)k * HW + (int64_t)i * a.W + j_out;
-                    __stcs(&a.ground[o], sEG[e]);
-                    __stcs(&a.ceil[o], sZC[e]);
-                    __stcs(&a.cost[o], cT[q]);
-                    a.mask[o] = (travbits >> q) & 1u;
+                    __stcs(gk + o, sEG[e]);
+                    __stcs(zk + o, sZC[e]);
+                    __stcs(tk + o, cT[q]);
+                    mk[o] = (travbits >> q) & 1u;
                 }
             }
         }
