@@ -489,11 +489,60 @@ k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ z
     else long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
 }
 
-// One warp per long segment.  Up to kLongStage heights are sorted by a
-// bitonic network in the warp's shared-memory buffer (padded with +inf);
-// longer segments, which no sensible cloud has, fall back to placing every
-// height at its rank (smaller heights, ties broken by index) from a copy in
-// global scratch.
+// Bitonic network over 32 * EPL heights held by one warp: element e * 32 +
+// lane in v[e] of that lane.  Partners 32 or more apart sit in the same
+// lane's registers; nearer ones are exchanged by shuffles.
+template <int EPL>
+__device__ __forceinline__ void warp_bitonic(float (&v)[EPL], int lane) {
+    constexpr int L = 32 * EPL;
+#pragma unroll
+    for (int size = 2; size <= L; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const int f = e ^ (stride >> 5);
+                    if (f > e) {
+                        const bool up = ((e * 32) & size) == 0;
+                        const float a = v[e], b = v[f];
+                        const float lo = fminf(a, b), hi = fmaxf(a, b);
+                        v[e] = up ? lo : hi;
+                        v[f] = up ? hi : lo;
+                    }
+                }
+            } else {
+                const bool lower = (lane & stride) == 0;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const float y = __shfl_xor_sync(0xffffffffu, v[e], stride);
+                    const bool up = ((e * 32 + lane) & size) == 0;
+                    v[e] = lower == up ? fminf(v[e], y) : fmaxf(v[e], y);
+                }
+            }
+        }
+    }
+}
+
+// One segment of n <= 32 * EPL heights sorted by one warp in registers
+// (coalesced loads and stores, padded with +inf).
+template <int EPL>
+__device__ __forceinline__ void warp_sort_segment(float *__restrict__ zs, int32_t s, int32_t n,
+                                                  int lane) {
+    float v[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) v[e] = e * 32 + lane < n ? zs[s + e * 32 + lane] : INFINITY;
+    warp_bitonic<EPL>(v, lane);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e)
+        if (e * 32 + lane < n) zs[s + e * 32 + lane] = v[e];
+}
+
+// One warp per long segment.  Up to 256 heights are sorted in the warp's
+// registers; up to kLongStage by the same network in the warp's shared-memory
+// buffer (padded with +inf); longer segments, which no sensible cloud has,
+// fall back to placing every height at its rank (smaller heights, ties
+// broken by index) from a copy in global scratch.
 constexpr int kLongStage = 1024;
 
 __global__ void __launch_bounds__(kThreads)
@@ -507,7 +556,11 @@ k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
     for (int t = blockIdx.x * (kThreads / 32) + wib; t < total; t += gridDim.x * (kThreads / 32)) {
         const int32_t c = long_cells[t];
         const int32_t s = start[c], n = start[c + 1] - s;
-        if (n <= kLongStage) {
+        if (n <= 32) warp_sort_segment<1>(zs, s, n, lane);
+        else if (n <= 64) warp_sort_segment<2>(zs, s, n, lane);
+        else if (n <= 128) warp_sort_segment<4>(zs, s, n, lane);
+        else if (n <= 256) warp_sort_segment<8>(zs, s, n, lane);
+        else if (n <= kLongStage) {
             int L = 32;
             while (L < n) L <<= 1;
             for (int i = lane; i < L; i += 32) buf[i] = i < n ? zs[s + i] : INFINITY;
@@ -543,6 +596,15 @@ k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
             __syncwarp();
         }
     }
+}
+
+// Blocks of k_sort_long: one resident wave (four 32 KB blocks per SM), each
+// warp taking long segments in turn.
+int long_sort_blocks() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 4 * sms;
 }
 
 __global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices) {
@@ -636,8 +698,8 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
     k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<grid_blocks(m, kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
-                                                                    ws.long_count, ws.long_cells);
+    k_sort_long<<<long_sort_blocks(), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                        ws.long_count, ws.long_cells);
     count_launches(n > 0 ? 9 : 7);
     return cudaGetLastError();
 }
@@ -682,8 +744,8 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
     cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
     k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<grid_blocks(m, kThreads), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
-                                                              ws.long_count, ws.long_cells);
+    k_sort_long<<<long_sort_blocks(), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                        ws.long_count, ws.long_cells);
     count_launches(launches);
     return cudaGetLastError();
 }
