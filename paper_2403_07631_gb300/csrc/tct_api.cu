@@ -27,7 +27,7 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     L.partial = o; o = align_up(o + 4 * (nb + 1));
     L.zs = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
     L.scratch = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
-    L.long_count = o; o = align_up(o + 4);
+    L.long_count = o; o = align_up(o + 8);
     L.long_cells = o; o = align_up(o + 4 * (n_points > 0 ? m : 0));
     L.zkeys = o; o = align_up(o + 4 * 2);
     L.upre = o; o = align_up(o + 4 * (TCT_MAX_SLICES + 1));

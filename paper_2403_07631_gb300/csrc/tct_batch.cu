@@ -39,7 +39,7 @@ BatchLayout batch_layout(const tct_map *maps, int n_maps) {
     L.partial = o; o = align256(o + 4 * (nb + 1));
     L.zs = o; o = align256(o + 4 * (size_t)points);
     L.scratch = o; o = align256(o + 4 * (size_t)points);
-    L.long_count = o; o = align256(o + 4);
+    L.long_count = o; o = align256(o + 8);
     L.long_cells = o; o = align256(o + 4 * (size_t)cells);
     L.queue = o; o = align256(o + 4);
     L.zkeys = o; o = align256(o + 8 * (size_t)n_maps);

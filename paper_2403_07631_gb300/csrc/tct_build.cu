@@ -442,8 +442,11 @@ k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restric
 }
 
 // Sort each cell's segment ascending.  Segments of up to 16 heights are
-// sorted in registers by a bitonic network (padded with +inf); longer ones
-// are queued for k_sort_long.
+// sorted in registers by a bitonic network (padded with +inf); segments of
+// up to kWarpSort heights are queued for k_sort_long (from the front of
+// long_cells, counted in long_count[0]), longer ones for k_sort_huge (from
+// the back, counted in long_count[1]).
+constexpr int kWarpSort = 256;
 template <int L>
 __device__ __forceinline__ void bitonic_sort(float (&v)[L]) {
 #pragma unroll
@@ -486,7 +489,8 @@ k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ z
     if (n <= 4) sort_segment<4>(zs, s, n);
     else if (n <= 8) sort_segment<8>(zs, s, n);
     else if (n <= 16) sort_segment<16>(zs, s, n);
-    else long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
+    else if (n <= kWarpSort) long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
+    else long_cells[m - 1 - atomicAdd(long_count + 1, 1)] = (int32_t)c;
 }
 
 // Bitonic network over 32 * EPL heights held by one warp: element e * 32 +
@@ -538,53 +542,65 @@ __device__ __forceinline__ void warp_sort_segment(float *__restrict__ zs, int32_
         if (e * 32 + lane < n) zs[s + e * 32 + lane] = v[e];
 }
 
-// One warp per long segment.  Up to 256 heights are sorted in the warp's
-// registers; up to kLongStage by the same network in the warp's shared-memory
-// buffer (padded with +inf); longer segments, which no sensible cloud has,
-// fall back to placing every height at its rank (smaller heights, ties
-// broken by index) from a copy in global scratch.
-constexpr int kLongStage = 1024;
-
+// One warp per long segment (17 .. kWarpSort heights), sorted in the warp's
+// registers.
 __global__ void __launch_bounds__(kThreads)
 k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
-            float *__restrict__ scratch, const int32_t *__restrict__ long_count,
-            const int32_t *__restrict__ long_cells) {
-    __shared__ float stage[kThreads / 32][kLongStage];
+            const int32_t *__restrict__ long_count, const int32_t *__restrict__ long_cells) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int total = *long_count;
-    float *buf = stage[wib];
+    const int total = long_count[0];
     for (int t = blockIdx.x * (kThreads / 32) + wib; t < total; t += gridDim.x * (kThreads / 32)) {
         const int32_t c = long_cells[t];
         const int32_t s = start[c], n = start[c + 1] - s;
         if (n <= 32) warp_sort_segment<1>(zs, s, n, lane);
         else if (n <= 64) warp_sort_segment<2>(zs, s, n, lane);
         else if (n <= 128) warp_sort_segment<4>(zs, s, n, lane);
-        else if (n <= 256) warp_sort_segment<8>(zs, s, n, lane);
-        else if (n <= kLongStage) {
-            int L = 32;
+        else warp_sort_segment<8>(zs, s, n, lane);
+    }
+}
+
+// One block per huge segment (more than kWarpSort heights).  Up to kHugeStage
+// heights are sorted by a bitonic network in shared memory (padded with
+// +inf), a barrier between its steps; longer segments, which no sensible
+// cloud has, fall back to placing every height at its rank (smaller heights,
+// ties broken by index) from a copy in global scratch.
+constexpr int kHugeThreads = 512;
+constexpr int kHugeStage = 8192;
+
+__global__ void __launch_bounds__(kHugeThreads)
+k_sort_huge(const int32_t *__restrict__ start, float *__restrict__ zs,
+            float *__restrict__ scratch, const int32_t *__restrict__ long_count,
+            const int32_t *__restrict__ long_cells, int64_t m) {
+    __shared__ float buf[kHugeStage];
+    const int tid = threadIdx.x;
+    const int total = long_count[1];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int32_t c = long_cells[m - 1 - t];
+        const int32_t s = start[c], n = start[c + 1] - s;
+        if (n <= kHugeStage) {
+            int L = 2 * kWarpSort;
             while (L < n) L <<= 1;
-            for (int i = lane; i < L; i += 32) buf[i] = i < n ? zs[s + i] : INFINITY;
-            __syncwarp();
+            for (int i = tid; i < L; i += kHugeThreads) buf[i] = i < n ? zs[s + i] : INFINITY;
+            __syncthreads();
             for (int size = 2; size <= L; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int i = lane; i < L; i += 32) {
-                        const int jx = i ^ stride;
-                        if (jx > i) {
-                            const float x = buf[i], y = buf[jx];
-                            const bool up = (i & size) == 0;
-                            if ((x > y) == up) { buf[i] = y; buf[jx] = x; }
-                        }
+                    // pair k compares i = 2 stride (k / stride) + k % stride with i + stride
+                    for (int k = tid; k < L / 2; k += kHugeThreads) {
+                        const int i = 2 * stride * (k / stride) + k % stride, jx = i + stride;
+                        const float x = buf[i], y = buf[jx];
+                        const bool up = (i & size) == 0;
+                        if ((x > y) == up) { buf[i] = y; buf[jx] = x; }
                     }
-                    __syncwarp();
+                    __syncthreads();
                 }
             }
-            for (int i = lane; i < n; i += 32) zs[s + i] = buf[i];
-            __syncwarp();
+            for (int i = tid; i < n; i += kHugeThreads) zs[s + i] = buf[i];
+            __syncthreads();
         } else {
-            for (int i = lane; i < n; i += 32) scratch[s + i] = zs[s + i];
-            __syncwarp();
+            for (int i = tid; i < n; i += kHugeThreads) scratch[s + i] = zs[s + i];
+            __syncthreads();
             const float *src = scratch + s;
-            for (int i = lane; i < n; i += 32) {
+            for (int i = tid; i < n; i += kHugeThreads) {
                 const float z = src[i];
                 int32_t rank = 0;
                 for (int j = 0; j < n; ++j) {
@@ -593,18 +609,17 @@ k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
                 }
                 zs[s + rank] = z;
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
 }
 
-// Blocks of k_sort_long: one resident wave (four 32 KB blocks per SM), each
-// warp taking long segments in turn.
-int long_sort_blocks() {
+// Blocks of the two long-segment sorts: one resident wave each.
+int sm_count() {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return 4 * sms;
+    return sms;
 }
 
 __global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices) {
@@ -695,12 +710,13 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     if (n > 0)
         k_scatter<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                    ws.start, ws.zs);
-    cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(ws.long_count, 0, 2 * sizeof(int32_t), s);
     k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<long_sort_blocks(), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
-                                                        ws.long_count, ws.long_cells);
-    count_launches(n > 0 ? 9 : 7);
+    k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);
+    k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch, ws.long_count,
+                                                        ws.long_cells, m);
+    count_launches(n > 0 ? 10 : 8);
     return cudaGetLastError();
 }
 
@@ -728,7 +744,7 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
     const int64_t m = total_cells;
     cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int32_t) * m, s);
     if (e != cudaSuccess) return e;
-    int launches = 5;
+    int launches = 6;
     if (blocks > 0) {
         k_count_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt);
         ++launches;
@@ -741,11 +757,12 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
         k_scatter_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.zs);
         ++launches;
     }
-    cudaMemsetAsync(ws.long_count, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(ws.long_count, 0, 2 * sizeof(int32_t), s);
     k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<long_sort_blocks(), kThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
-                                                        ws.long_count, ws.long_cells);
+    k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);
+    k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch, ws.long_count,
+                                                        ws.long_cells, m);
     count_launches(launches);
     return cudaGetLastError();
 }

@@ -36,8 +36,8 @@ struct Workspace {
     int32_t *partial;   // [n_scan_blocks + 1]
     float *zs;          // [P]    point heights grouped by cell, sorted per cell
     float *scratch;     // [P]    copy of very long segments while they are sorted
-    int32_t *long_count;  // [1]  cells whose segment needs the warp sort
-    int32_t *long_cells;  // [HW] their indices
+    int32_t *long_count;  // [2]  cells queued for the warp sort, for the block sort
+    int32_t *long_cells;  // [HW] their indices (warp sort from the front, block sort from the back)
     int32_t *zkeys;     // [2]    ordered-int min / max z of the finite points
     int32_t *upre;      // [128]  per slice: bits [0, upre) of the uniqueness row set
     uint32_t *ubits;    // [128][4] per slice: further uniqueness bits

@@ -268,15 +268,16 @@ def test_many_slices_dense_changes(seed):
 
 
 def test_long_cell_segments():
-    # cells holding 20, 50, 100, 200, 300 and 3000 points (vertical scan
-    # lines): the per-thread networks, the warp register sorts of 32, 64, 128
-    # and 256 heights, the shared-memory sort and the rank sort all run
+    # cells holding 20, 50, 100, 200, 300, 3000 and 9000 points (vertical
+    # scan lines): the per-thread networks, the warp register sorts of 32, 64,
+    # 128 and 256 heights, the block sort in shared memory and the rank sort
+    # all run
     rng = np.random.default_rng(31)
     base = np.stack([rng.uniform(0, 4.0, 30_000), rng.uniform(0, 4.0, 30_000),
                      rng.normal(0, 0.01, 30_000)], 1)
     cols = []
     for (x, y, m) in ((1.05, 1.05, 20), (1.55, 3.05, 50), (2.55, 3.55, 100), (3.55, 0.55, 200),
-                      (2.05, 1.55, 300), (3.05, 2.55, 3000)):
+                      (2.05, 1.55, 300), (3.05, 2.55, 3000), (0.55, 3.55, 9000)):
         z = rng.uniform(0.0, 6.0, m)
         z[: m // 10] = np.round(z[: m // 10], 1)          # repeated heights
         cols.append(np.stack([np.full(m, x), np.full(m, y), z], 1))
