@@ -18,7 +18,8 @@
 //      changed;
 //   4. re-inflates (Eq. 6) a warp's 32 x 8 strip only when a c^init in its
 //      window changed, otherwise keeps the previous c^T (bit-identical
-//      inputs give bit-identical results), and accumulates the uniqueness
+//      inputs give bit-identical results; when few strips changed, their
+//      halves are spread over all warps), and accumulates the uniqueness
 //      bits, reading earlier costs back only for cells whose run holds a
 //      higher cost than the current one,
 // and writes all four layers of every slice.  Work follows the changes,
