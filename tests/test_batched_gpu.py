@@ -206,3 +206,40 @@ def test_build_then_evaluate_batched_equal_single_calls():
         np.testing.assert_array_equal(m.cost.cpu().numpy(), one["cost"])
         np.testing.assert_array_equal(m.mask.cpu().numpy(), one["mask"])
         np.testing.assert_array_equal(m.keep.cpu().numpy(), one["keep"])
+
+
+def _scan_lines(seed, lines):
+    """A 40 x 40 cloud with vertical scan lines: cells holding the given numbers of points."""
+    rng = np.random.default_rng(seed)
+    base = np.stack([rng.uniform(0, 4.0, 20_000), rng.uniform(0, 4.0, 20_000),
+                     rng.normal(0, 0.01, 20_000)], 1)
+    cols = []
+    for (x, y, m) in lines:
+        z = rng.uniform(0.0, 6.0, m)
+        z[: m // 10] = np.round(z[: m // 10], 1)          # repeated heights
+        cols.append(np.stack([np.full(m, x), np.full(m, y), z], 1))
+    return np.concatenate([base] + cols).astype(np.float32)
+
+
+def test_batch_long_segments_in_every_sort_class():
+    """Cells of 20 to 9000 points in two maps of one batch go through the warp
+    sorts (queued from the front of the shared list) and the block and rank
+    sorts (queued from its back): every map's layers equal the single-map
+    path's and the oracle's."""
+    pts = [_scan_lines(41, ((1.05, 1.05, 20), (1.55, 3.05, 50), (2.55, 3.55, 100),
+                            (3.55, 0.55, 200), (2.05, 1.55, 300), (3.05, 2.55, 3000))),
+           _scan_lines(42, ((0.55, 3.55, 9000), (1.25, 0.35, 700), (3.35, 1.85, 130)))]
+    grids = [tct.Grid(0.0, 0.0, 0.1, 40, 40, 0.5, 13, 0.0, True) for _ in pts]
+    maps = [tct.MapBuffers.allocate(torch.from_numpy(p).cuda(), g) for p, g in zip(pts, grids)]
+    ws = torch.empty(tct.tct_workspace_bytes_batched(maps, PARAMS_ROBOT), dtype=torch.uint8,
+                     device="cuda")
+    tct.tct_build_evaluate_batched(maps, PARAMS_ROBOT, ws, None)
+    torch.cuda.synchronize()
+    for p, g, m in zip(pts, grids, maps):
+        got = _host(m)
+        one = P.gpu_build_evaluate(p, g, PARAMS_ROBOT)
+        for key in ("ground", "ceil", "cost", "mask", "keep"):
+            np.testing.assert_array_equal(got[key], one[key], err_msg=key)
+        ref = P.oracle_all(p, g, PARAMS_ROBOT)
+        P.assert_equal_layers(got["ground"], ref["ground"], "ground")
+        P.assert_equal_layers(got["ceil"], ref["ceil"], "ceiling")
