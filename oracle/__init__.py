@@ -17,7 +17,8 @@ out.  Every function cites the passage of the paper it restates:
                        initial costs, inflation, traversable mask)
 - ``simplify``         Sec. III-C, Eq. 7-9 (sequential slice-removal chain)
 - ``sample``           the cost / elevation queries C(q), e^G(q) of Eq. 10 (bilinear,
-                       with the gradient of the interpolant)
+                       with the gradient of the interpolant); ``sample_f64`` at
+                       FP64 query coordinates
 - ``refine``           descent on path waypoints with those queries (an objective of ours)
 """
 from __future__ import annotations
@@ -85,11 +86,12 @@ def _load():
                                         P, P, P, P, P, P]
         lib.oracle_simplify.argtypes = [i32, i32, i32, P, P, P, ctypes.c_double, i32, P, P, P]
         lib.oracle_sample.argtypes = [ctypes.POINTER(OracleGrid), P, i32, P, P, i64, P, P]
+        lib.oracle_sample_f64.argtypes = [ctypes.POINTER(OracleGrid), P, i32, P, P, i64, P, P]
         lib.oracle_refine.argtypes = [ctypes.POINTER(OracleGrid), P, P, i32, i32, i32,
                                       ctypes.c_double, ctypes.c_double, P]
         for f in ("oracle_plane_heights", "oracle_bounds", "oracle_derive_grid", "oracle_build",
                   "oracle_kernel", "oracle_evaluate", "oracle_simplify", "oracle_sample",
-                  "oracle_refine"):
+                  "oracle_sample_f64", "oracle_refine"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -246,6 +248,21 @@ def sample(g: Grid, layer: np.ndarray, xy: np.ndarray, slice_idx: np.ndarray,
     grad = np.empty((q, 2), np.float64)
     _check(_load().oracle_sample(ctypes.byref(g.c()), _ptr(layer), int(is_ground), _ptr(xy),
                                  _ptr(sl), q, _ptr(out), _ptr(grad)), "sample")
+    return out, grad
+
+
+def sample_f64(g: Grid, layer: np.ndarray, xy: np.ndarray, slice_idx: np.ndarray,
+               is_ground: bool = False):
+    """``sample`` at FP64 query coordinates (for central differences whose step
+    lies below a float32 ulp of the coordinate)."""
+    layer = np.ascontiguousarray(layer, np.float32)
+    xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+    sl = np.ascontiguousarray(slice_idx, np.int32).reshape(-1)
+    q = len(xy)
+    out = np.empty(q, np.float64)
+    grad = np.empty((q, 2), np.float64)
+    _check(_load().oracle_sample_f64(ctypes.byref(g.c()), _ptr(layer), int(is_ground), _ptr(xy),
+                                     _ptr(sl), q, _ptr(out), _ptr(grad)), "sample_f64")
     return out, grad
 
 

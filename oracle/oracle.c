@@ -538,44 +538,63 @@ static double oracle_layer_at(const float *L, int W, int i, int j, double fill)
     return v > -INFINITY ? v : fill;
 }
 
+/* One query at (x, y) on slice k; grad may be NULL. */
+static void sample_one(const oracle_grid *g, const float *layer, int32_t is_ground, double x,
+                       double y, int k, double *out, double *grad)
+{
+    const int W = g->W, H = g->H;
+    const int64_t HW = (int64_t)W * H;
+    const double r = (double)g->res;
+    if (k < 0 || k >= g->N || !isfinite(x) || !isfinite(y)) {
+        *out = NAN;
+        if (grad) grad[0] = grad[1] = NAN;
+        return;
+    }
+    const double fill = is_ground ? (double)plane_height(g, k) - (double)g->d_s : 0.0;
+    const float *L = layer + (int64_t)k * HW;
+    double u = (x - (double)g->x0) / r - 0.5, v = (y - (double)g->y0) / r - 0.5;
+    int cu = 0, cv = 0;                     /* clamped along x / y */
+    if (u < 0.0) { u = 0.0; cu = 1; }
+    if (u > W - 1) { u = W - 1; cu = 1; }
+    if (v < 0.0) { v = 0.0; cv = 1; }
+    if (v > H - 1) { v = H - 1; cv = 1; }
+    int j0 = (int)floor(u), i0 = (int)floor(v);
+    if (j0 > W - 2) j0 = W - 2;
+    if (i0 > H - 2) i0 = H - 2;
+    if (j0 < 0) j0 = 0;
+    if (i0 < 0) i0 = 0;
+    const int j1 = W > 1 ? j0 + 1 : j0, i1 = H > 1 ? i0 + 1 : i0;
+    const double fu = W > 1 ? u - j0 : 0.0, fv = H > 1 ? v - i0 : 0.0;
+    const double c00 = oracle_layer_at(L, W, i0, j0, fill), c01 = oracle_layer_at(L, W, i0, j1, fill);
+    const double c10 = oracle_layer_at(L, W, i1, j0, fill), c11 = oracle_layer_at(L, W, i1, j1, fill);
+    *out = (1 - fu) * (1 - fv) * c00 + fu * (1 - fv) * c01 + (1 - fu) * fv * c10 + fu * fv * c11;
+    if (grad) {
+        grad[0] = (cu || W < 2) ? 0.0 : ((1 - fv) * (c01 - c00) + fv * (c11 - c10)) / r;
+        grad[1] = (cv || H < 2) ? 0.0 : ((1 - fu) * (c10 - c00) + fu * (c11 - c01)) / r;
+    }
+}
+
+/* Queries at float32 coordinates (the precision the library takes them in). */
 int oracle_sample(const oracle_grid *g, const float *layer, int32_t is_ground, const float *xy,
                   const int32_t *slice, int64_t q, double *out, double *grad)
 {
     if (!g || !layer || !xy || !slice || !out || q < 0) return ORACLE_EINVAL;
-    const int W = g->W, H = g->H;
-    const int64_t HW = (int64_t)W * H;
-    const double r = (double)g->res;
-    for (int64_t t = 0; t < q; ++t) {
-        const double x = xy[2 * t], y = xy[2 * t + 1];
-        const int k = slice[t];
-        if (k < 0 || k >= g->N || !isfinite(x) || !isfinite(y)) {
-            out[t] = NAN;
-            if (grad) grad[2 * t] = grad[2 * t + 1] = NAN;
-            continue;
-        }
-        const double fill = is_ground ? (double)plane_height(g, k) - (double)g->d_s : 0.0;
-        const float *L = layer + (int64_t)k * HW;
-        double u = (x - (double)g->x0) / r - 0.5, v = (y - (double)g->y0) / r - 0.5;
-        int cu = 0, cv = 0;                     /* clamped along x / y */
-        if (u < 0.0) { u = 0.0; cu = 1; }
-        if (u > W - 1) { u = W - 1; cu = 1; }
-        if (v < 0.0) { v = 0.0; cv = 1; }
-        if (v > H - 1) { v = H - 1; cv = 1; }
-        int j0 = (int)floor(u), i0 = (int)floor(v);
-        if (j0 > W - 2) j0 = W - 2;
-        if (i0 > H - 2) i0 = H - 2;
-        if (j0 < 0) j0 = 0;
-        if (i0 < 0) i0 = 0;
-        const int j1 = W > 1 ? j0 + 1 : j0, i1 = H > 1 ? i0 + 1 : i0;
-        const double fu = W > 1 ? u - j0 : 0.0, fv = H > 1 ? v - i0 : 0.0;
-        const double c00 = oracle_layer_at(L, W, i0, j0, fill), c01 = oracle_layer_at(L, W, i0, j1, fill);
-        const double c10 = oracle_layer_at(L, W, i1, j0, fill), c11 = oracle_layer_at(L, W, i1, j1, fill);
-        out[t] = (1 - fu) * (1 - fv) * c00 + fu * (1 - fv) * c01 + (1 - fu) * fv * c10 + fu * fv * c11;
-        if (grad) {
-            grad[2 * t] = (cu || W < 2) ? 0.0 : ((1 - fv) * (c01 - c00) + fv * (c11 - c10)) / r;
-            grad[2 * t + 1] = (cv || H < 2) ? 0.0 : ((1 - fu) * (c10 - c00) + fu * (c11 - c01)) / r;
-        }
-    }
+    for (int64_t t = 0; t < q; ++t)
+        sample_one(g, layer, is_ground, (double)xy[2 * t], (double)xy[2 * t + 1], slice[t],
+                   out + t, grad ? grad + 2 * t : NULL);
+    return ORACLE_OK;
+}
+
+/* The same queries at FP64 coordinates (finite differences with steps far
+ * below a float32 ulp of the coordinate). */
+int oracle_sample_f64(const oracle_grid *g, const float *layer, int32_t is_ground,
+                      const double *xy, const int32_t *slice, int64_t q, double *out,
+                      double *grad)
+{
+    if (!g || !layer || !xy || !slice || !out || q < 0) return ORACLE_EINVAL;
+    for (int64_t t = 0; t < q; ++t)
+        sample_one(g, layer, is_ground, xy[2 * t], xy[2 * t + 1], slice[t], out + t,
+                   grad ? grad + 2 * t : NULL);
     return ORACLE_OK;
 }
 

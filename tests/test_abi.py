@@ -87,6 +87,11 @@ def test_host_only_calls(lib):
     assert p["c_b"] == 50.0 and p["patch_radius"] == 2
     g = tct.tct_plan_grid([0.0, 0.0, -0.0499, 19.99, 19.95, 5.84], 0.1, 0.5)
     assert (g.W, g.H, g.n_slices) == (200, 200, 12)
+    # the hand-worked cell edges of the oracle's pin (r_g = 0.25, exact): a
+    # maximum on the left edge of cell 8 opens it, one just inside does not
+    for (xmax, ymax, W, H) in ((2.0, 0.75, 9, 4), (1.99, 0.7499, 8, 3), (0.25, 0.0, 2, 1)):
+        g = tct.tct_plan_grid([0.0, 0.0, 0.0, xmax, ymax, 0.3], 0.25, 0.5)
+        assert (g.x0, g.y0, g.W, g.H, g.n_slices) == (0.0, 0.0, W, H, 1)
     with pytest.raises(tct.TctError):
         tct.tct_plan_grid([0.0, 0.0, 0.0, 1.0, 1.0, 1000.0], 0.1, 0.5)   # N > 127
     n = tct.tct_workspace_bytes(tct.Grid(0.0, 0.0, 0.1, 1000, 1000, 0.5, 40), 5_000_000)

@@ -172,6 +172,29 @@ def test_derive_grid_two_storey_building(oracle_mod):
     assert g.x0 == sc.points[:, 0].min() and g.y0 == sc.points[:, 1].min()
 
 
+@pytest.mark.parametrize("xmax,ymax,W,H", [
+    (2.0, 0.75, 9, 4),          # maxima exactly on a cell edge: they open cells 8 and 3
+    (1.99, 0.7499, 8, 3),       # just inside: the last cells are 7 and 2
+    (0.25, 0.0, 2, 1),          # one edge past the origin; a line of points along x
+])
+def test_derive_grid_width_height_at_cell_edges(oracle_mod, xmax, ymax, W, H):
+    """Sec. III-A: the grid starts at the cloud's minimum and its last column
+    and row hold the maximum.  With r_g = 0.25 (exact in binary) the cell of
+    a coordinate is floor(x / 0.25) by hand: x = 2.0 lies on the left edge of
+    cell 8, so W = 9; x = 1.99 lies in cell 7, so W = 8."""
+    pts = np.array([[0.0, 0.0, 0.0], [xmax, ymax, 0.3], [xmax / 2, ymax / 3, 0.1]], np.float32)
+    g = oracle_mod.derive_grid(pts, 0.25, 0.5)
+    assert (g.x0, g.y0) == (0.0, 0.0)
+    assert (g.W, g.H) == (W, H)
+    # every point of the cloud lands on the grid, the maximum in the last cell
+    eG, _, _, dropped, _ = oracle_mod.build(pts, g, zmin_from_data=True)
+    assert dropped == 0
+    assert eG[0, H - 1, W - 1] == np.float32(0.3)
+    # shifted origin: the same widths with the cloud moved by (-1.5, +2.25)
+    g2 = oracle_mod.derive_grid(pts + np.array([-1.5, 2.25, 0.0], np.float32), 0.25, 0.5)
+    assert (g2.x0, g2.y0, g2.W, g2.H) == (-1.5, 2.25, W, H)
+
+
 def test_nonfinite_points_are_rejected(oracle_mod):
     pts = np.array([[0.05, 0.05, 0.0], [np.nan, 0.05, 1.0], [0.05, np.inf, 1.0],
                     [0.05, 0.05, -np.inf]], np.float32)

@@ -143,6 +143,36 @@ def test_staircase_step_cost(oracle_mod, theta_p, edge_cost):
             assert np.all(cG[rows, j] == 0.0)
 
 
+@pytest.mark.parametrize("axis", ["rows", "columns"])
+def test_step_cost_patch_at_the_map_border(oracle_mod, axis):
+    """The p_s patch of Eq. 4 (our reading R8): the (2R_p+1)^2 - 1 = 24
+    neighbours without the centre; a neighbour off the map counts as not
+    gentle and stays in the denominator.  On the staircase above, a step-edge
+    cell in the interior sees 15 gentle neighbours (p_s = 15/24).  One cell
+    from the map border, its patch loses the off-map line (5 cells) and the
+    border line (no central difference there, so not gentle): 3 gentle
+    columns on 3 lines, p_s = 9/24 = 0.375.  Two cells from the border only
+    the border line is lost: 12/24 = 0.5.  theta_p = 0.37 separates 9/24 from
+    9/25 (a patch that counted the centre), theta_p = 0.45 separates 9/24
+    from 9/19 (a patch that dropped off-map neighbours from the
+    denominator)."""
+    eG = _staircase(16, 32)
+    if axis == "columns":
+        eG = np.ascontiguousarray(eG.T)
+    for theta_p, near1 in ((0.37, 5.0), (0.45, 50.0)):
+        p = dict(PARAMS_ROBOT, theta_p=theta_p)
+        cT, mask, frag, aux = _eval(oracle_mod, eG, np.full_like(eG, INF), p)
+        cG = aux[3, 0] if axis == "rows" else aux[3, 0].T
+        n = cG.shape[0]
+        for j in range(4, 28):
+            if j % 4 not in (0, 3):
+                continue
+            # one line from either border: 9/24; two lines: 12/24; interior 15/24
+            np.testing.assert_allclose([cG[1, j], cG[n - 2, j]], near1, rtol=1e-6)
+            np.testing.assert_allclose([cG[2, j], cG[n - 3, j], cG[7, j]], 5.0, rtol=1e-6)
+        assert np.all(frag == 0)
+
+
 def _golden_fig3():
     rows = []
     with open(os.path.join(GOLDEN, "fig3_inflation.txt")) as f:

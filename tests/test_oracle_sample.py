@@ -58,26 +58,39 @@ def test_invalid_ground_reads_plane_below(oracle_mod):
 
 
 def test_gradient_matches_central_differences(oracle_mod):
+    """The analytic gradient of the interpolant against FP64 central
+    differences (h = 1e-4 m) of the oracle's own values at FP64 coordinates,
+    at the sampler tolerance |g - fd| <= 1e-5 max(|fd|, c^B / r_g).  Queries
+    within 2h of a lattice line are skipped (the interpolant has a kink
+    there); elsewhere it is linear along each axis, so the difference is
+    exact up to FP64 rounding and a dropped term, a wrong corner or a wrong
+    sign would show far above the tolerance."""
     rng = np.random.default_rng(3)
     H, W = 20, 25
     layer = rng.uniform(0, 50, (2, H, W)).astype(np.float32)
     g = _grid(oracle_mod, H, W, N=2)
     h = 1e-4
     xy = np.stack([rng.uniform(0.1, 2.4, 300), rng.uniform(0.1, 1.9, 300)], 1)
-    # skip queries within 2h of a lattice line (the interpolant has kinks there)
     u = xy / 0.1 - 0.5
     ok = (np.abs(u - np.round(u)) > 2 * h / 0.1).all(1)
     xy = xy[ok]
     sl = rng.integers(0, 2, len(xy))
-    _, grad = oracle_mod.sample(g, layer, xy, sl)
-    # the query is taken in float32; difference in float64 coordinates stays exact enough
+    _, grad = oracle_mod.sample_f64(g, layer, xy, sl)
     fd = np.zeros_like(grad)
     for a in range(2):
         e = np.zeros(2); e[a] = h
-        vp, _ = oracle_mod.sample(g, layer, xy + e, sl)
-        vm, _ = oracle_mod.sample(g, layer, xy - e, sl)
+        vp, _ = oracle_mod.sample_f64(g, layer, xy + e, sl)
+        vm, _ = oracle_mod.sample_f64(g, layer, xy - e, sl)
         fd[:, a] = (vp - vm) / (2 * h)
-    np.testing.assert_allclose(grad, fd, rtol=2e-2, atol=50.0 / 0.1 * 2e-3)
+    scale = np.maximum(np.abs(fd), 50.0 / 0.1)
+    assert np.all(np.abs(grad - fd) <= 1e-5 * scale)
+    assert np.abs(grad - fd).max() < 1e-8 * 500      # FP64 rounding only
+    # the float32-coordinate entry reads the same values at float32 points
+    x32 = xy.astype(np.float32)
+    v32, g32 = oracle_mod.sample(g, layer, x32, sl)
+    v64, g64 = oracle_mod.sample_f64(g, layer, x32.astype(np.float64), sl)
+    np.testing.assert_array_equal(v32, v64)
+    np.testing.assert_array_equal(g32, g64)
 
 
 def test_refinement_descends_smooth_bowl(oracle_mod):
