@@ -10,7 +10,10 @@ Tolerances (written here once, used by every parity test):
 - traversable mask: exact on cells whose mask is pinned (fragile bit 1 clear);
 - keep flags: exact against the oracle's chain run on the GPU's own layers
   (the decision in float32, as the kernel takes it), and exact against the
-  oracle's own layers whenever the oracle reports the chain robust.
+  oracle's own layers whenever the oracle reports the chain robust;
+- fragile cells (left out of the cost and mask checks) must stay rare: every
+  cost check also bounds their fraction by FRAGILE_MAX and prints it, so an
+  oracle that marked too many cells fragile could not make a check vacuous.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ import oracle
 from paper_2403_07631_gb300 import tct
 
 COST_RTOL = 1e-5
+FRAGILE_MAX = 1e-3
 
 
 def oracle_params(p: dict) -> dict:
@@ -93,7 +97,20 @@ def oracle_all(points: np.ndarray, grid: tct.Grid, params: dict):
                 dropped=dropped, nonfinite=bad, grid=og)
 
 
-def assert_costs(cost_gpu: np.ndarray, cost_ref: np.ndarray, fragile: np.ndarray):
+def fragile_fraction(fragile: np.ndarray, max_frac: float | None = FRAGILE_MAX) -> float:
+    """Share of the cells the oracle leaves out of the checks; printed, and
+    bounded by max_frac unless that is None (a caller bounding a total)."""
+    n = int(np.count_nonzero(fragile))
+    frac = n / max(fragile.size, 1)
+    print(f"fragile cells: {n} of {fragile.size} ({frac:.2e})")
+    if max_frac is not None:
+        assert frac <= max_frac, f"{n} of {fragile.size} cells fragile, above {max_frac}"
+    return frac
+
+
+def assert_costs(cost_gpu: np.ndarray, cost_ref: np.ndarray, fragile: np.ndarray,
+                 max_fragile: float | None = FRAGILE_MAX):
+    fragile_fraction(fragile, max_fragile)
     ok = (fragile & 1) == 0
     err = np.abs(cost_gpu.astype(np.float64) - cost_ref)
     lim = COST_RTOL * np.maximum(1.0, np.abs(cost_ref))

@@ -83,7 +83,8 @@ def test_stress_windows_match_oracle(stress):
         where = f"window rows {i_lo}:{i_hi} cols {j_lo}:{j_hi}"
         P.assert_equal_layers(stress["ground"][win].cpu().numpy(), eG, "ground, " + where)
         P.assert_equal_layers(stress["ceil"][win].cpu().numpy(), eC, "ceiling, " + where)
-        P.assert_costs(stress["cost"][win].cpu().numpy()[core], cT[core], frag[core])
+        P.assert_costs(stress["cost"][win].cpu().numpy()[core], cT[core], frag[core],
+                         max_fragile=None)
         P.assert_masks(stress["mask"][win].cpu().numpy()[core], mask[core], frag[core])
         n_cells += frag[core].size
         n_fragile += int((frag[core] != 0).sum())
