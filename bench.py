@@ -27,6 +27,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# The benchmark robot, written out here (not read from the library) so that
+# the reference arm never loads the CUDA library: Table I of the paper
+# (d_min 0.5, d_ref 0.65, theta_b 1.70, theta_p 0.20, c^B 50, alpha_d 20,
+# alpha_b 20, alpha_s 15), a maximum slope of 30 deg (theta_s = tan 30 deg),
+# an inflation radius d_inf = 0.3 m with the Fig. 3 safe margin d_sm = 0.4 m,
+# and a 5 x 5 p_s patch.
+ROBOT_PARAMS = dict(d_min=0.5, d_ref=0.65, theta_b=1.70, theta_s=0.5773502691896257,
+                    theta_p=0.20, c_b=50.0, alpha_d=20.0, alpha_b=20.0, alpha_s=15.0,
+                    d_inf=0.3, d_sm=0.4, patch_radius=2, flags=0)
+
 METRIC = "tomogram build+eval Mpoints/s & slice-cells/s, % HBM roofline; batched vs plain"
 UNIT = "Mpoints/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -231,21 +241,13 @@ def sampler_paths(dev, grid, params, cost, ground, mask, stats, steps, paths=256
     random traversable cells of the most traversable kept slice plus N(0, 0.2 m)
     noise.  Times the query + adjoint kernels and the fused refinement."""
     import torch
-    from paper_2403_07631_gb300 import tct
+    from paper_2403_07631_gb300 import scenes, tct
     st = tct.stats_from(stats)
     g = tct.Grid(grid.x0, grid.y0, grid.res, grid.W, grid.H, grid.d_s, grid.n_slices,
                  float(st.z_min), True)
     k = int(max(range(grid.n_slices), key=lambda i: st.trav_cells[i]))
-    gen = torch.Generator(device="cpu").manual_seed(4)
-    cells = torch.nonzero(mask[k].reshape(-1)).reshape(-1).cpu()
-    pick = cells[torch.randint(len(cells), (paths, 2), generator=gen)]
-    ij = torch.stack([pick // grid.W, pick % grid.W], -1).double()          # [paths, 2, (i, j)]
-    ends = torch.stack([grid.x0 + (ij[..., 1] + 0.5) * grid.res,
-                        grid.y0 + (ij[..., 0] + 0.5) * grid.res], -1)       # [paths, 2, (x, y)]
-    t = torch.linspace(0, 1, L, dtype=torch.float64)[None, :, None]
-    xy = ends[:, :1] * (1 - t) + ends[:, 1:] * t
-    xy[:, 1:-1] += 0.2 * torch.randn(paths, L - 2, 2, generator=gen, dtype=torch.float64)
-    xy = xy.float().contiguous().to(dev)
+    xy = torch.from_numpy(scenes.straight_paths(mask[k].cpu().numpy() != 0, grid.x0, grid.y0,
+                                                grid.res, paths, L)).to(dev)
     sl = torch.full((paths, L), k, dtype=torch.int32, device=dev)
     q = paths * L
     c_out = torch.empty(paths, L, device=dev)
@@ -563,15 +565,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from paper_2403_07631_gb300 import tct
-    tct_params = None
-    try:
-        tct_params = tct.robot_params()
-    except Exception:
-        import math
-        tct_params = dict(d_min=0.5, d_ref=0.65, theta_b=1.7, theta_s=math.tan(math.radians(30)),
-                          theta_p=0.2, c_b=50.0, alpha_d=20.0, alpha_b=20.0, alpha_s=15.0,
-                          d_inf=0.3, d_sm=0.4, patch_radius=2)
+    tct_params = dict(ROBOT_PARAMS)
     sc = workload(args.workload)
     times = []
     for i in range(args.warmup + args.steps):
@@ -609,7 +603,7 @@ def main():
     dev = torch.device("cuda", local)
     libbuild.build()
 
-    params = tct.robot_params()
+    params = dict(ROBOT_PARAMS)
     sc = workload(args.workload)
     P, N, H, W = len(sc.points), sc.n_slices, sc.H, sc.W
     grid = tct.Grid(sc.x0, sc.y0, sc.res, W, H, sc.d_s, N, 0.0, True)
