@@ -576,6 +576,11 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
 #pragma unroll
                 for (int q = 0; q < kStrip; ++q) acc[q] = slots[(2 * rank * (kStrip / 2) + q) * 32 + lane];
             }
+            // the next slice's listing (step 1a) writes this region before its
+            // first barrier: every owner has read its slots before any warp
+            // passes here (the branch is uniform over the CTA: dmask was read
+            // after a barrier)
+            __syncthreads();
         } else if (need_infl) {
             inflate_column<RK, kStrip, G::CW>(sCI + tr0 * G::CW + ts, c, acc);
         }
