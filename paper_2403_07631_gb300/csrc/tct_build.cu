@@ -561,11 +561,46 @@ k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
 
 // One block per huge segment (more than kWarpSort heights).  Up to kHugeStage
 // heights are sorted by a bitonic network in shared memory (padded with
-// +inf), a barrier between its steps; longer segments, which no sensible
-// cloud has, fall back to placing every height at its rank (smaller heights,
-// ties broken by index) from a copy in global scratch.
+// +inf), a barrier between its steps.  Longer segments (a cloud that puts
+// most of its points in one cell: invalid returns written as the origin, a
+// dense pole) are cut into chunks of kHugeStage heights, each sorted the
+// same way in place, and the sorted runs are then merged pairwise, doubling
+// their length per pass, between the segment and its copy in global scratch:
+// every height finds its output position from its index in its own run and
+// a binary search in the partner run (strictly smaller heights of the right
+// run before it, equal or smaller ones of the left run before a right one),
+// so a pass costs O(n log n) and the whole sort O(n log^2 n).
 constexpr int kHugeThreads = 512;
 constexpr int kHugeStage = 8192;
+
+// Sorts buf[0, L) ascending, L a power of two; called by the whole block.
+__device__ void block_bitonic(float *buf, int L) {
+    const int tid = threadIdx.x;
+    for (int size = 2; size <= L; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            // pair k compares i = 2 stride (k / stride) + k % stride with i + stride
+            for (int k = tid; k < L / 2; k += kHugeThreads) {
+                const int i = 2 * stride * (k / stride) + k % stride, jx = i + stride;
+                const float x = buf[i], y = buf[jx];
+                const bool up = (i & size) == 0;
+                if ((x > y) == up) { buf[i] = y; buf[jx] = x; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sorts the n heights at seg (global memory) through buf; whole block.
+__device__ void block_sort_chunk(float *__restrict__ seg, int32_t n, float *buf) {
+    const int tid = threadIdx.x;
+    int L = 2 * kWarpSort;
+    while (L < n) L <<= 1;
+    for (int i = tid; i < L; i += kHugeThreads) buf[i] = i < n ? seg[i] : INFINITY;
+    __syncthreads();
+    block_bitonic(buf, L);
+    for (int i = tid; i < n; i += kHugeThreads) seg[i] = buf[i];
+    __syncthreads();
+}
 
 __global__ void __launch_bounds__(kHugeThreads)
 k_sort_huge(const int32_t *__restrict__ start, float *__restrict__ zs,
@@ -578,37 +613,40 @@ k_sort_huge(const int32_t *__restrict__ start, float *__restrict__ zs,
         const int32_t c = long_cells[m - 1 - t];
         const int32_t s = start[c], n = start[c + 1] - s;
         if (n <= kHugeStage) {
-            int L = 2 * kWarpSort;
-            while (L < n) L <<= 1;
-            for (int i = tid; i < L; i += kHugeThreads) buf[i] = i < n ? zs[s + i] : INFINITY;
-            __syncthreads();
-            for (int size = 2; size <= L; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    // pair k compares i = 2 stride (k / stride) + k % stride with i + stride
-                    for (int k = tid; k < L / 2; k += kHugeThreads) {
-                        const int i = 2 * stride * (k / stride) + k % stride, jx = i + stride;
-                        const float x = buf[i], y = buf[jx];
-                        const bool up = (i & size) == 0;
-                        if ((x > y) == up) { buf[i] = y; buf[jx] = x; }
+            block_sort_chunk(zs + s, n, buf);
+            continue;
+        }
+        for (int64_t c0 = 0; c0 < n; c0 += kHugeStage)
+            block_sort_chunk(zs + s + c0, (int32_t)min((int64_t)kHugeStage, (int64_t)n - c0), buf);
+        float *src = zs + s, *dst = scratch + s;
+        for (int64_t w = kHugeStage; w < n; w *= 2) {
+            for (int64_t i = tid; i < n; i += kHugeThreads) {
+                const int64_t run = i / w, a0 = (run & ~(int64_t)1) * w;
+                const int64_t a1 = min(a0 + w, (int64_t)n), b1 = min(a0 + 2 * w, (int64_t)n);
+                const float x = src[i];
+                int64_t lo, hi, pos;
+                if ((run & 1) == 0) {
+                    lo = a1; hi = b1;                       // right run: heights < x
+                    while (lo < hi) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (src[mid] < x) lo = mid + 1; else hi = mid;
                     }
-                    __syncthreads();
+                    pos = i + (lo - a1);
+                } else {
+                    lo = a0; hi = a1;                       // left run: heights <= x
+                    while (lo < hi) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (src[mid] <= x) lo = mid + 1; else hi = mid;
+                    }
+                    pos = a0 + (i - a1) + (lo - a0);
                 }
+                dst[pos] = x;
             }
-            for (int i = tid; i < n; i += kHugeThreads) zs[s + i] = buf[i];
             __syncthreads();
-        } else {
-            for (int i = tid; i < n; i += kHugeThreads) scratch[s + i] = zs[s + i];
-            __syncthreads();
-            const float *src = scratch + s;
-            for (int i = tid; i < n; i += kHugeThreads) {
-                const float z = src[i];
-                int32_t rank = 0;
-                for (int j = 0; j < n; ++j) {
-                    const float y = src[j];
-                    rank += (y < z) || (y == z && j < i);
-                }
-                zs[s + rank] = z;
-            }
+            float *tmp = src; src = dst; dst = tmp;
+        }
+        if (src != zs + s) {
+            for (int64_t i = tid; i < n; i += kHugeThreads) zs[s + i] = src[i];
             __syncthreads();
         }
     }

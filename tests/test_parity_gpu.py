@@ -174,6 +174,18 @@ def test_evaluate_random_layers(params):
     _evaluate_check(eG, eC, params)
 
 
+@pytest.mark.parametrize("theta_p", [0.37, 0.45])
+def test_evaluate_step_patch_at_the_map_border(theta_p):
+    # the oracle's border pin of the p_s patch (off-map neighbours count as
+    # not gentle and stay in the denominator): a staircase whose step edges
+    # run into the top and bottom borders (slice 0) and, transposed, into the
+    # left and right borders (slice 1)
+    j = np.arange(32)[None, :]
+    st = np.broadcast_to((0.17 * (j // 4)).astype(np.float32), (32, 32))
+    eG = np.ascontiguousarray(np.stack([st, st.T])).astype(np.float32)
+    _evaluate_check(eG, np.full_like(eG, np.inf), dict(PARAMS_ROBOT, theta_p=theta_p))
+
+
 def test_evaluate_fine_resolution_radius_12():
     # r_g = 0.05 m: D_inf = 6, D_sm = 7, a 25 x 25 window
     rng = np.random.default_rng(12)
@@ -270,8 +282,8 @@ def test_many_slices_dense_changes(seed):
 def test_long_cell_segments():
     # cells holding 20, 50, 100, 200, 300, 3000 and 9000 points (vertical
     # scan lines): the per-thread networks, the warp register sorts of 32, 64,
-    # 128 and 256 heights, the block sort in shared memory and the rank sort
-    # all run
+    # 128 and 256 heights, the block sort in shared memory and the chunked
+    # block sort with merge passes all run
     rng = np.random.default_rng(31)
     base = np.stack([rng.uniform(0, 4.0, 30_000), rng.uniform(0, 4.0, 30_000),
                      rng.normal(0, 0.01, 30_000)], 1)
@@ -284,6 +296,35 @@ def test_long_cell_segments():
     pts = np.concatenate([base] + cols).astype(np.float32)
     grid = tct.Grid(0.0, 0.0, 0.1, 40, 40, 0.5, 13, 0.0, True)
     _full_check(pts, grid, PARAMS_ROBOT)
+
+
+def test_huge_cell_segment_time_bound():
+    # one cell holding a million points (a LiDAR's invalid returns written as
+    # one position, a dense pole) and one holding 20 001: the chunked block
+    # sort with merge passes, O(n log^2 n), must finish well inside a second
+    import time
+    rng = np.random.default_rng(33)
+    base = np.stack([rng.uniform(0, 2.4, 20_000), rng.uniform(0, 2.4, 20_000),
+                     rng.normal(0, 0.01, 20_000)], 1)
+    cols = []
+    for (x, y, m) in ((1.05, 1.05, 1_000_000), (0.35, 2.05, 20_001)):
+        z = rng.uniform(0.0, 6.0, m)
+        z[: m // 4] = np.round(z[: m // 4], 2)           # many repeated heights
+        cols.append(np.stack([np.full(m, x), np.full(m, y), z], 1))
+    pts = np.concatenate([base] + cols).astype(np.float32)
+    grid = tct.Grid(0.0, 0.0, 0.1, 24, 24, 0.5, 13, 0.0, True)
+    g, r = _full_check(pts, grid, PARAMS_ROBOT)
+    dev = torch.device("cuda")
+    d = torch.from_numpy(pts).to(dev)
+    ws, ground, ceil, cost, mask, keep, stats = tct.alloc_outputs(grid, len(pts), dev,
+                                                                  PARAMS_ROBOT)
+    tct.tct_build_evaluate(d, grid, PARAMS_ROBOT, ws, ground, ceil, cost, mask, keep, stats)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tct.tct_build_evaluate(d, grid, PARAMS_ROBOT, ws, ground, ceil, cost, mask, keep, stats)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 1.0
+    np.testing.assert_array_equal(ground.cpu().numpy(), r["ground"])
 
 
 @pytest.mark.parametrize("kept_only", [False, True])
