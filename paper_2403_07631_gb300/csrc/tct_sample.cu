@@ -5,11 +5,15 @@
 // A query (x, y, k) interpolates slice k bilinearly on the lattice of cell
 // centres: u = (x - x0)/r_g - 1/2, v = (y - y0)/r_g - 1/2, clamped to the
 // grid; the 2x2 stencil starts at (min(floor v, H-2), min(floor u, W-2)).
-// The coordinate transform is done in FP64 (two operations per query): in
-// float32 the cell fraction of a point 100 m from the origin would carry an
-// error of 6e-5 cells, 3e-3 in a cost of 50.  Interpolation and gradients are
-// float32.  Invalid ground (-inf) reads as h_k - d_s.  Along an axis where
-// the query was clamped the gradient is zero.
+// The coordinate transform stays in float32 without losing the cell
+// fraction: x - x0 is formed exactly as an unevaluated sum hi + lo (Knuth's
+// TwoSum), the cell is estimated from hi / r_g and the remainder
+// x - x0 - (j + 1/2) r_g is taken from hi, lo and the exact error of the
+// product (j + 1/2) r_g (one fma); a plain float32 u would carry an error of
+// 6e-5 cells 100 m from the origin (3e-3 in a cost of 50), this one about
+// 1e-7 cells.  Interpolation and gradients are float32.  Invalid ground
+// (-inf) reads as h_k - d_s.  Along an axis where the query was clamped the
+// gradient is zero.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -21,7 +25,7 @@ namespace {
 constexpr int kThreads = 256;
 
 struct SampleGeo {
-    double x0, y0, res;
+    float x0, y0, res;
     float inv_res, d_s, z_min;
     int32_t W, H, N;
 };
@@ -47,22 +51,52 @@ struct Stencil {
     bool cu, cv;         // clamped along x / y
 };
 
+// One axis of the transform u = (x - x0) / r - 1/2 on n cells: the first
+// stencil cell j0, the fraction f in [0, 1] and whether u was clamped to
+// [0, n-1] (as the FP64 definition clamps it).
+__device__ __forceinline__ void locate_axis(float x, float x0, float r, float inv_r, int n,
+                                            int &j0, float &f, bool &clamped) {
+    // TwoSum: hi + lo == x - x0 exactly
+    const float nx0 = -x0;
+    const float hi = __fadd_rn(x, nx0);
+    const float xv = __fsub_rn(hi, nx0);
+    const float nv = __fsub_rn(hi, xv);
+    const float lo = __fadd_rn(__fsub_rn(x, xv), __fsub_rn(nx0, nv));
+    // cell estimate, then the remainder d - (j + 1/2) r with the exact
+    // rounding error of the product
+    const float q = __fmul_rn(hi, inv_r);
+    int j = (int)floorf(__fsub_rn(q, 0.5f));
+    j = max(-2, min(j, n + 1));
+    float rem = 0.0f;
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        const float t = (float)j + 0.5f;
+        const float p = __fmul_rn(t, r);
+        const float pe = __fmaf_rn(t, r, -p);
+        rem = __fadd_rn(__fsub_rn(hi, p), __fsub_rn(lo, pe));
+        if (rem < 0.0f) --j;
+        else if (rem >= r) ++j;
+        else break;
+    }
+    clamped = false;
+    if (j < 0) {                                   // u < 0
+        j0 = 0; f = 0.0f; clamped = true;
+    } else if (j > n - 1 || (j == n - 1 && rem > 0.0f)) {   // u > n - 1
+        j0 = n - 2; f = 1.0f; clamped = true;
+    } else {
+        j0 = j; f = fminf(__fmul_rn(rem, inv_r), 1.0f);
+        if (j0 > n - 2) { j0 = n - 2; f = 1.0f; }  // u == n - 1 exactly
+    }
+    if (n < 2) { j0 = 0; f = 0.0f; }
+}
+
 __device__ __forceinline__ Stencil locate(const SampleGeo &g, float x, float y, int k) {
-    double u = ((double)x - g.x0) / g.res - 0.5;
-    double v = ((double)y - g.y0) / g.res - 0.5;
     Stencil s;
-    s.cu = s.cv = false;
-    if (u < 0.0) { u = 0.0; s.cu = true; }
-    if (u > g.W - 1) { u = g.W - 1; s.cu = true; }
-    if (v < 0.0) { v = 0.0; s.cv = true; }
-    if (v > g.H - 1) { v = g.H - 1; s.cv = true; }
-    int j0 = (int)floor(u), i0 = (int)floor(v);
-    j0 = max(0, min(j0, g.W - 2));
-    i0 = max(0, min(i0, g.H - 2));
+    int j0, i0;
+    locate_axis(x, g.x0, g.res, g.inv_res, g.W, j0, s.fu, s.cu);
+    locate_axis(y, g.y0, g.res, g.inv_res, g.H, i0, s.fv, s.cv);
     s.dj = g.W > 1 ? 1 : 0;
     s.di = g.H > 1 ? g.W : 0;
-    s.fu = g.W > 1 ? (float)(u - j0) : 0.0f;
-    s.fv = g.H > 1 ? (float)(v - i0) : 0.0f;
     s.base = (int64_t)k * g.W * g.H + (int64_t)i0 * g.W + j0;
     return s;
 }
