@@ -365,7 +365,9 @@ int tct_autotune_batched(const tct_map *h_maps, int32_t n_maps, const tct_params
  * not), and otherwise exactly what tct_build_evaluate returns.  It calls no
  * allocation routine.  The first call on a device looks up the array's device
  * address (with that device current) and should come before any stream
- * capture.  Every call uses the same array and leaves its contents behind;
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or any teardown of the device's primary context) it is
+ * stale, so do not call this entry point on that device again.  Every call uses the same array and leaves its contents behind;
  * the call clears what it needs zeroed itself.  Calls that overlap on the GPU
  * race on the array: serialise them.
  */

@@ -416,3 +416,24 @@ def cave_terrain(seed: int = 5, n_points: int = 60_000_000, side_cells: int = 40
                  pts, 0.0, 0.0, res, side_cells, side_cells, 0.5, 80,
                  dict(seed=seed, n_tunnels=n_tunnels, n_shelves=n_shelves,
                       tunnel_points=tunnel_points))
+
+
+# ------------------------------------------------------------ query paths
+
+def straight_paths(walkable: np.ndarray, x0: float, y0: float, res: float, paths: int = 256,
+                   length: int = 512, seed: int = 4, noise: float = 0.2) -> np.ndarray:
+    """Waypoint paths for the cost queries: `paths` straight lines of `length`
+    waypoints between random cells of the boolean [H, W] map `walkable`
+    (cell centres), the interior waypoints jittered by N(0, noise) metres.
+    Returns float32 [paths, length, 2] world (x, y)."""
+    rng = np.random.default_rng(seed)
+    H, W = walkable.shape
+    cells = np.flatnonzero(walkable.reshape(-1))
+    if len(cells) == 0:
+        raise ValueError("no walkable cell to start or end a path on")
+    pick = cells[rng.integers(0, len(cells), (paths, 2))]
+    ends = np.stack([x0 + (pick % W + 0.5) * res, y0 + (pick // W + 0.5) * res], -1)
+    t = np.linspace(0.0, 1.0, length)[None, :, None]
+    xy = ends[:, :1] * (1 - t) + ends[:, 1:] * t
+    xy[:, 1:-1] += noise * rng.standard_normal((paths, length - 2, 2))
+    return xy.astype(np.float32)
