@@ -67,7 +67,7 @@ struct Geo {
 
 // Shared state of the per-slice counters, kept in static shared memory.
 struct SliceCounters {
-    int32_t nlist[2];                  // cells a plane passed, slices of even / odd k
+    int32_t nlist[3];                  // cells a plane passed, slice k in nlist[k % 3]
     int32_t nwork[2];                  // dirty row blocks: gentle flags, c^init
     uint32_t infl;                     // warps whose strip is re-inflated this slice
     int32_t upre[TCT_MAX_SLICES + 1];
@@ -178,7 +178,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     constexpr uint32_t kGentHi = (1u << (2 * RP)) - 1u;
     constexpr uint32_t kWinHi = (1u << (2 * RK)) - 1u;
 
-    if (tid < 2) counters.nlist[tid] = 0;
+    if (tid < 3) counters.nlist[tid] = 0;
     if (tid == 0) counters.infl = 0;
     for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
         s_upre[i] = 0;
@@ -321,8 +321,15 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         // ---- 1. grounds and ceilings: advance the pointers past h ----
         // 1a. list the cells whose next height the plane passed: four cells a
         //     thread (one 16-byte load), one shared counter add per warp
-        int32_t *nlist = &counters.nlist[k & 1];
-        if (tid == 0) counters.nwork[0] = counters.nwork[1] = 0;   // read before the last barrier
+        // three counters in turn: the next slice's is cleared here, where the
+        // last reader of its previous use (two slices back) has passed the
+        // previous barrier, and before this slice's barrier, past which the
+        // next slice's listing may start (a quiet slice has no other barrier)
+        int32_t *nlist = &counters.nlist[k % 3];
+        if (tid == 0) {
+            counters.nwork[0] = counters.nwork[1] = 0;   // read before the last barrier
+            counters.nlist[(k + 1) % 3] = 0;
+        }
         for (int base = 0; base < G::NE / 4; base += kNT) {
             const int e4 = base + tid;
             float4 z = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
@@ -345,10 +352,16 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         }
         __syncthreads();
         if (tid == 0) counters.infl = 0;   // last read before this barrier
+        // A quiet slice (no plane passed a height of the region) changes no
+        // ground, ceiling, gentle flag, c^init or c^T: it only writes the
+        // layers again, with no uniqueness bit (Eq. 9 fails against an
+        // identical slice) and the counts of the slice before.
+        const int n_pass = *nlist;
+        const bool quiet = !first && n_pass == 0;
         // 1b. advance the listed cells, spread evenly over the threads; each
         //     round reads the next four heights of the segment at once, so a
         //     cell that passes n heights waits for ceil(n / 4) loads, not n
-        const int n_pass = *nlist;
+        if (!quiet) {
         for (int t = tid; t < n_pass; t += kNT) {
             const int e = sList[t];
             const int r = e / G::EW, s = e - r * G::EW;
@@ -378,14 +391,16 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
         }
         __syncthreads();
+        }
 
         // the next slice's change words are cleared here, a barrier ahead of their use
         {
             uint32_t *nG = sChgG0 + ((k + 1) & 1) * G::EH * G::EWW;
             uint32_t *nC = sChgC0 + ((k + 1) & 1) * G::EH * G::EWW;
             for (int i = tid; i < G::EH * G::EWW; i += kNT) { nG[i] = 0; nC[i] = 0; }
-            if (tid == 0) counters.nlist[(k + 1) & 1] = 0;
         }
+
+        if (!quiet) {
 
         // ---- 2. gentle flags (Eq. 2: m^grad < theta_s) ----
         // 2a. one lane per 32-column row block: the block is dirty when a
@@ -633,6 +648,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             wvalid = (int)__reduce_add_sync(0xffffffffu, (uint32_t)__popc(validbits & inmap));
             wtrav = (int)__reduce_add_sync(0xffffffffu, (uint32_t)__popc(travbits & inmap));
         }
+        }   // !quiet
         if (lane == 0) {
             if (wvalid) atomicAdd(&s_valid[k], wvalid);
             if (wtrav) atomicAdd(&s_trav[k], wtrav);
