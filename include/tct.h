@@ -360,7 +360,7 @@ int tct_autotune_batched(const tct_map *h_maps, int32_t n_maps, const tct_params
  * The scratch is a fixed array of TCT_NOALLOC_SCRATCH_BYTES inside the
  * library, held by every GPU that loads the library until the process exits.
  * Returns TCT_ERR_WORKSPACE_TOO_SMALL when tct_workspace_bytes(grid, n,
- * params) exceeds it (about 12 bytes per cell plus 8 per point: the 200 x 200,
+ * params) exceeds it (about 12 bytes per cell plus 10 per point: the 200 x 200,
  * 200k-point building fits, the 1000 x 1000, 5M-point parking structure does
  * not), and otherwise exactly what tct_build_evaluate returns.  It calls no
  * allocation routine.  The first call on a device looks up the array's device

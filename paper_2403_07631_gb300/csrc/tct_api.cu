@@ -14,7 +14,8 @@ namespace {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cnt, start, partial, zs, scratch, long_count, long_cells, zkeys, upre, ubits, stats, queue, total;
+    size_t cnt, start, partial, zs, scratch, bucket_l, bcur, long_count, long_cells, zkeys, upre, ubits,
+        stats, queue, total;
 };
 
 Layout layout(const tct_grid &g, int64_t n_points) {
@@ -23,11 +24,13 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     Layout L;
     size_t o = 0;
     L.cnt = o; o = align_up(o + 4 * m);
+    L.bcur = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_buckets((int64_t)m) : 0));
+    L.long_count = o; o = align_up(o + 8);
     L.start = o; o = align_up(o + 4 * (m + 1));
     L.partial = o; o = align_up(o + 4 * (nb + 1));
     L.zs = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
     L.scratch = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_points : 0));
-    L.long_count = o; o = align_up(o + 8);
+    L.bucket_l = o; o = align_up(o + 2 * (size_t)(n_points > 0 ? n_points : 0));
     L.long_cells = o; o = align_up(o + 4 * (n_points > 0 ? m : 0));
     L.zkeys = o; o = align_up(o + 4 * 2);
     L.upre = o; o = align_up(o + 4 * (TCT_MAX_SLICES + 1));
@@ -87,6 +90,8 @@ Workspace carve(void *base, const tct_grid &g, int64_t n_points) {
     w.partial = reinterpret_cast<int32_t *>(b + L.partial);
     w.zs = reinterpret_cast<float *>(b + L.zs);
     w.scratch = reinterpret_cast<float *>(b + L.scratch);
+    w.bucket_l = reinterpret_cast<uint16_t *>(b + L.bucket_l);
+    w.bcur = reinterpret_cast<int32_t *>(b + L.bcur);
     w.long_count = reinterpret_cast<int32_t *>(b + L.long_count);
     w.long_cells = reinterpret_cast<int32_t *>(b + L.long_cells);
     w.zkeys = reinterpret_cast<int32_t *>(b + L.zkeys);

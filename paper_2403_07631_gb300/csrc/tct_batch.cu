@@ -18,7 +18,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchLayout {
-    size_t cnt, start, partial, zs, scratch, long_count, long_cells, queue;
+    size_t cnt, start, partial, zs, scratch, bucket_l, bcur, long_count, long_cells, queue;
     size_t zkeys, upre, ubits, stats, total;
     int64_t cells, points;
 };
@@ -35,11 +35,13 @@ BatchLayout batch_layout(const tct_map *maps, int n_maps) {
     const size_t nb = (size_t)((cells + kScanTile - 1) / kScanTile);
     size_t o = 0;
     L.cnt = o; o = align256(o + 4 * (size_t)cells);
+    L.bcur = o; o = align256(o + 4 * (size_t)n_buckets(cells));
+    L.long_count = o; o = align256(o + 8);
     L.start = o; o = align256(o + 4 * ((size_t)cells + 1));
     L.partial = o; o = align256(o + 4 * (nb + 1));
     L.zs = o; o = align256(o + 4 * (size_t)points);
     L.scratch = o; o = align256(o + 4 * (size_t)points);
-    L.long_count = o; o = align256(o + 8);
+    L.bucket_l = o; o = align256(o + 2 * (size_t)points);
     L.long_cells = o; o = align256(o + 4 * (size_t)cells);
     L.queue = o; o = align256(o + 4);
     L.zkeys = o; o = align256(o + 8 * (size_t)n_maps);
@@ -143,6 +145,8 @@ int run_batch(const tct_map *maps, int n_maps, const tct_params *params, const t
     ws.partial = reinterpret_cast<int32_t *>(base + L.partial);
     ws.zs = reinterpret_cast<float *>(base + L.zs);
     ws.scratch = reinterpret_cast<float *>(base + L.scratch);
+    ws.bucket_l = reinterpret_cast<uint16_t *>(base + L.bucket_l);
+    ws.bcur = reinterpret_cast<int32_t *>(base + L.bcur);
     ws.long_count = reinterpret_cast<int32_t *>(base + L.long_count);
     ws.long_cells = reinterpret_cast<int32_t *>(base + L.long_cells);
     int32_t *queue = reinterpret_cast<int32_t *>(base + L.queue);
@@ -298,6 +302,8 @@ int run_build_batch(const tct_map *maps, int n_maps, int points_per_block, void 
     ws.partial = reinterpret_cast<int32_t *>(base + L.partial);
     ws.zs = reinterpret_cast<float *>(base + L.zs);
     ws.scratch = reinterpret_cast<float *>(base + L.scratch);
+    ws.bucket_l = reinterpret_cast<uint16_t *>(base + L.bucket_l);
+    ws.bcur = reinterpret_cast<int32_t *>(base + L.bcur);
     ws.long_count = reinterpret_cast<int32_t *>(base + L.long_count);
     ws.long_cells = reinterpret_cast<int32_t *>(base + L.long_cells);
     int32_t *zkeys = reinterpret_cast<int32_t *>(base + L.zkeys);

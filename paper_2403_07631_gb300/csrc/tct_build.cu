@@ -5,8 +5,15 @@
 //            L2 atomics, bounds of z (block-reduced ordered-int atomics),
 //            dropped / non-finite counts;
 //   scan     exclusive prefix of the histogram (three small kernels);
-//   scatter  second pass over the points: each z lands in its cell's segment;
-//   sort     each cell's segment is sorted by z (thread per cell).
+//   bucket   second pass over the points: each z, with its cell's place in
+//            its bucket of kBucket consecutive cells, is appended to the
+//            bucket's range of a staging array (the range of zs the bucket's
+//            cells occupy), one cursor atomic per warp when the warp's points
+//            share a bucket;
+//   sort     one block per bucket places the heights by cell and sorts the
+//            short segments in shared memory and writes the bucket back in
+//            one coalesced sweep; longer segments go to a warp (up to 256
+//            heights) or a block (beyond) in global memory.
 // A sorted segment answers every plane with one monotone pointer: the ground
 // of plane h is the last z <= h, the ceiling the first z > h.  The fused
 // per-tile evaluation (tct_stack.cu) consumes the segments directly;
@@ -180,75 +187,117 @@ __global__ void k_bounds_finish(float *out6, tct_stats *stats) {
     if (t == 5 && stats) stats->z_max = key_float(k);
 }
 
-// One point of a map: pass 1 (count) counts it in its cell and tallies the
-// bounds, pass 2 (scatter) writes its height into the cell's segment, taking
-// slots from the top down so that the counters return to zero.
-template <bool kScatter>
-__device__ __forceinline__ void visit_point(float x, float y, float z, const GridDev &g,
+// One point of a map in pass 1: counted in its cell, bounds and tallies.
+__device__ __forceinline__ void count_point(float x, float y, float z, const GridDev &g,
                                             int64_t cell_off, int32_t *__restrict__ cnt,
-                                            const int32_t *__restrict__ start,
-                                            float *__restrict__ zs, PointTally &t) {
+                                            PointTally &t) {
     if (!finite3(x, y, z)) {
-        if (!kScatter) ++t.nonfinite;
+        ++t.nonfinite;
         return;
     }
     z = fold_zero(z);
-    if (!kScatter) {
-        const int32_t k = float_key(z);
-        t.zlo = min(t.zlo, k);
-        t.zhi = max(t.zhi, k);
-    }
+    const int32_t k = float_key(z);
+    t.zlo = min(t.zlo, k);
+    t.zhi = max(t.zhi, k);
     const int cell = cell_of(g, x, y);
     if (cell < 0) {
-        if (!kScatter) ++t.dropped;
+        ++t.dropped;
         return;
     }
-    const int64_t gc = cell_off + cell;
-    if (!kScatter) {
-        cell_slot<false>(cnt, gc);
-    } else {
-        const int32_t slot = cell_slot<true>(cnt, gc);
-        zs[start[gc] + slot] = z;
+    cell_slot<false>(cnt, cell_off + cell);
+}
+
+// U points of each lane in pass 2.  Called by every active lane of the warp
+// at once (gc < 0: no point).  The points that share the bucket of the
+// warp's first valid point (most of them: the points of a scan line fall in
+// consecutive cells) append their height and their cell's place in the
+// bucket to the bucket's range of the staging arrays, with one atomic for
+// all of them; the bucket sort later fills their cells' segments from the
+// bottom.  Any other point (a cloud in no particular order) takes a slot
+// from the top of its own cell's segment with an atomic on that cell's
+// count, which few other points share, and is written to zs directly.
+template <int U>
+__device__ __forceinline__ void bucket_points(const int64_t (&gc)[U], const float (&z)[U],
+                                              const int32_t *__restrict__ start,
+                                              int32_t *__restrict__ cnt,
+                                              int32_t *__restrict__ bcur, float *__restrict__ bz,
+                                              uint16_t *__restrict__ bl, float *__restrict__ zs) {
+    const uint32_t act = __activemask();
+    const int lane = threadIdx.x & 31;
+    uint32_t vm[U];
+    int first = -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        vm[u] = __ballot_sync(act, gc[u] >= 0);
+        if (first < 0 && vm[u]) first = u;
+    }
+    if (first < 0) return;
+    const int src = __ffs(vm[first]) - 1;
+    int64_t mine = -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (u == first) mine = gc[u];
+    const int64_t b0 = __shfl_sync(act, mine, src) >> kBucketLog;
+    const int32_t pos0 = start[b0 << kBucketLog];        // issued before the atomics
+    uint32_t sm[U];
+    int n0 = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        sm[u] = __ballot_sync(act, gc[u] >= 0 && (gc[u] >> kBucketLog) == b0);
+        n0 += __popc(sm[u]);
+    }
+    int32_t base = 0;
+    if (lane == src) base = atomicAdd(&bcur[b0], n0);
+    // the other points: all their slot atomics, then their segment starts
+    int32_t dslot[U], dpos[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        dslot[u] = gc[u] >= 0 && !((sm[u] >> lane) & 1u) ? atomicSub(&cnt[gc[u]], 1) - 1 : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) dpos[u] = dslot[u] >= 0 ? start[gc[u]] + dslot[u] : 0;
+    base = __shfl_sync(act, base, src);
+    const uint32_t lt = (1u << lane) - 1u;
+    int run = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if ((sm[u] >> lane) & 1u) {
+            const int64_t pos = (int64_t)pos0 + base + run + __popc(sm[u] & lt);
+            bz[pos] = z[u];
+            bl[pos] = (uint16_t)(gc[u] & (kBucket - 1));
+        } else if (dslot[u] >= 0) {
+            zs[dpos[u]] = z[u];
+        }
+        run += __popc(sm[u]);
     }
 }
 
-// Pass 2 for four points at once, in phases: the four slot atomics, then the
-// four segment starts, then the four stores, so that the round trips of the
-// four points overlap instead of following one another.
-__device__ __forceinline__ void scatter4(const float (&p)[4][3], const GridDev &g, int64_t cell_off,
-                                         int32_t *__restrict__ cnt,
-                                         const int32_t *__restrict__ start,
-                                         float *__restrict__ zs) {
-    int64_t gc[4];
-    float z[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        gc[u] = -1;
-        z[u] = fold_zero(p[u][2]);
-        if (finite3(p[u][0], p[u][1], p[u][2])) {
-            const int cell = cell_of(g, p[u][0], p[u][1]);
-            if (cell >= 0) gc[u] = cell_off + cell;
-        }
-    }
-    int32_t slot[4], base[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) slot[u] = gc[u] >= 0 ? cell_slot<true>(cnt, gc[u]) : 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) base[u] = gc[u] >= 0 ? start[gc[u]] : 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (gc[u] >= 0) zs[base[u] + slot[u]] = z[u];
+__device__ __forceinline__ int64_t point_cell(float x, float y, const GridDev &g, int64_t cell_off) {
+    if (!finite3(x, y, 0.0f)) return -1;
+    const int cell = cell_of(g, x, y);
+    return cell < 0 ? -1 : cell_off + cell;
 }
 
 // Points [p0, p1) of one map, thread `tid` of `nthreads`: groups of four
-// with vector loads where the base allows, the ragged ends one by one.
-template <bool kScatter>
+// with vector loads where the base allows, the ragged ends one by one.  Pass
+// 1 (kBucketPass false) counts, pass 2 buckets.
+template <bool kBucketPass>
 __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int stride, bool vec,
                                             int64_t p0, int64_t p1, int64_t tid, int64_t nthreads,
                                             const GridDev &g, int64_t cell_off,
                                             int32_t *__restrict__ cnt,
                                             const int32_t *__restrict__ start,
-                                            float *__restrict__ zs, PointTally &t) {
+                                            int32_t *__restrict__ bcur, float *__restrict__ bz,
+                                            uint16_t *__restrict__ bl, float *__restrict__ zs,
+                                            PointTally &t) {
+    auto one = [&](float x, float y, float z) {
+        if (kBucketPass) {
+            const int64_t gc[1] = {finite3(x, y, z) ? point_cell(x, y, g, cell_off) : -1};
+            const float zz[1] = {fold_zero(z)};
+            bucket_points<1>(gc, zz, start, cnt, bcur, bz, bl, zs);
+        } else {
+            count_point(x, y, z, g, cell_off, cnt, t);
+        }
+    };
     int64_t q0 = 0, q1 = 0;
     if (vec) {
         q0 = (p0 + 3) / 4;
@@ -258,25 +307,32 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
     for (int64_t q = q0 + tid; q < q1; q += nthreads) {
         float p[4][3];
         load4(xyz, stride, q, p);
-        if (kScatter) {
-            scatter4(p, g, cell_off, cnt, start, zs);
+        if (kBucketPass) {
+            int64_t gc[4];
+            float zz[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                gc[u] = finite3(p[u][0], p[u][1], p[u][2]) ? point_cell(p[u][0], p[u][1], g, cell_off)
+                                                            : -1;
+                zz[u] = fold_zero(p[u][2]);
+            }
+            bucket_points<4>(gc, zz, start, cnt, bcur, bz, bl, zs);
         } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                visit_point<false>(p[u][0], p[u][1], p[u][2], g, cell_off, cnt, start, zs, t);
+            for (int u = 0; u < 4; ++u) one(p[u][0], p[u][1], p[u][2]);
         }
     }
     const int64_t a1 = vec ? min(4 * q0, p1) : p1;
     for (int64_t i = p0 + tid; i < a1; i += nthreads) {
         float p[3];
         load1(xyz, stride, i, p);
-        visit_point<kScatter>(p[0], p[1], p[2], g, cell_off, cnt, start, zs, t);
+        one(p[0], p[1], p[2]);
     }
     if (vec) {
         for (int64_t i = max(4 * q1, p0) + tid; i < p1; i += nthreads) {
             float p[3];
             load1(xyz, stride, i, p);
-            visit_point<kScatter>(p[0], p[1], p[2], g, cell_off, cnt, start, zs, t);
+            one(p[0], p[1], p[2]);
         }
     }
 }
@@ -288,18 +344,20 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
     PointTally t;
     t.init();
     visit_range<false>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                       (int64_t)gridDim.x * blockDim.x, g, 0, cnt, nullptr, nullptr, t);
+                       (int64_t)gridDim.x * blockDim.x, g, 0, cnt, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, t);
     flush_tally(t, zkeys, stats, true);
 }
 
 // Pass 2 of one map.
 __global__ void __launch_bounds__(kThreads)
-k_scatter(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
-          int32_t *__restrict__ cnt, const int32_t *__restrict__ start, float *__restrict__ zs) {
+k_bucket(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
+         int32_t *__restrict__ cnt, const int32_t *__restrict__ start, int32_t *__restrict__ bcur,
+         float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs) {
     PointTally t;
     t.init();
     visit_range<true>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                      (int64_t)gridDim.x * blockDim.x, g, 0, cnt, start, zs, t);
+                      (int64_t)gridDim.x * blockDim.x, g, 0, cnt, start, bcur, bz, bl, zs, t);
 }
 
 // Both passes over a batch: block b serves one chunk of one map's points.
@@ -334,20 +392,21 @@ k_count_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt)
     PointTally t;
     t.init();
     visit_range<false>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
-                       m.cell_off, cnt, nullptr, nullptr, t);
+                       m.cell_off, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, t);
     flush_tally(t, m.zkeys, m.stats, true);
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_scatter_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt,
-                  const int32_t *__restrict__ start, float *__restrict__ zs) {
+k_bucket_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt,
+                 const int32_t *__restrict__ start, int32_t *__restrict__ bcur,
+                 float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs) {
     const PointMap &m = b.maps[batch_map_of_block(b)];
     const int64_t p0 = (int64_t)((int)blockIdx.x - m.block_start) * b.chunk;
     const int64_t p1 = min(m.n, p0 + b.chunk);
     PointTally t;
     t.init();
     visit_range<true>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
-                      m.cell_off, cnt, start, zs, t);
+                      m.cell_off, cnt, start, bcur, bz, bl, zs, t);
 }
 
 // Exclusive scan of cnt[0, m) into start[0, m], in tiles of kScanTile.
@@ -479,18 +538,71 @@ __device__ __forceinline__ void sort_segment(float *__restrict__ zs, int32_t s, 
         if (i < n) zs[s + i] = v[i];
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_sort_cells(const int32_t *__restrict__ start, int64_t m, float *__restrict__ zs,
-             int32_t *__restrict__ long_count, int32_t *__restrict__ long_cells) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
-    const int32_t s = start[c], n = start[c + 1] - s;
+// Pass 3: one block per bucket of kBucket cells.  The bucket's staged
+// heights sit in the staging arrays at the start of the range of zs its
+// cells occupy; the heights written directly already fill the top of their
+// cells' segments in zs.  The block reads the range of zs into shared
+// memory, places each staged height at its cell's next slot from the bottom
+// (shared-memory cursors), sorts segments of up to 16 heights in registers
+// and writes the range back.  When the bucket holds more than kBucketStage
+// heights the same happens in global memory.  Segments of 17 .. kWarpSort
+// heights are queued for k_sort_long (from the front of long_cells, counted
+// in long_count[0]), longer ones for k_sort_huge (from the back,
+// long_count[1]).
+constexpr int kBucketStage = 8192;
+
+__device__ __forceinline__ void sort_or_queue(float *seg, int32_t n, int64_t cell, int64_t m,
+                                              int32_t *__restrict__ long_count,
+                                              int32_t *__restrict__ long_cells) {
     if (n <= 1) return;
-    if (n <= 4) sort_segment<4>(zs, s, n);
-    else if (n <= 8) sort_segment<8>(zs, s, n);
-    else if (n <= 16) sort_segment<16>(zs, s, n);
-    else if (n <= kWarpSort) long_cells[atomicAdd(long_count, 1)] = (int32_t)c;
-    else long_cells[m - 1 - atomicAdd(long_count + 1, 1)] = (int32_t)c;
+    if (n <= 4) sort_segment<4>(seg, 0, n);
+    else if (n <= 8) sort_segment<8>(seg, 0, n);
+    else if (n <= 16) sort_segment<16>(seg, 0, n);
+    else if (n <= kWarpSort) long_cells[atomicAdd(long_count, 1)] = (int32_t)cell;
+    else long_cells[m - 1 - atomicAdd(long_count + 1, 1)] = (int32_t)cell;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bucket_sort(const int32_t *__restrict__ start, int64_t m, const int32_t *__restrict__ bcur,
+              const float *__restrict__ bz, const uint16_t *__restrict__ bl,
+              float *__restrict__ zs, int32_t *__restrict__ long_count,
+              int32_t *__restrict__ long_cells) {
+    __shared__ int32_t s_off[kBucket + 1];
+    __shared__ int32_t s_cur[kBucket];
+    __shared__ float s_z[kBucketStage];
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x << kBucketLog;
+    const int ncell = (int)min((int64_t)kBucket, m - c0);
+    const int32_t z0 = start[c0];
+    const int32_t staged = bcur[blockIdx.x];
+    for (int l = tid; l <= ncell; l += kThreads) s_off[l] = start[c0 + l] - z0;
+    for (int l = tid; l < ncell; l += kThreads) s_cur[l] = 0;
+    __syncthreads();
+    const int32_t nb = s_off[ncell];
+    if (nb == 0) return;
+    if (nb <= kBucketStage) {
+        if (staged < nb)
+            for (int32_t i = tid; i < nb; i += kThreads) s_z[i] = zs[z0 + i];
+        __syncthreads();
+        for (int32_t i = tid; i < staged; i += kThreads) {
+            const int l = bl[z0 + i];
+            s_z[s_off[l] + atomicAdd(&s_cur[l], 1)] = bz[z0 + i];
+        }
+        __syncthreads();
+        for (int l = tid; l < ncell; l += kThreads)
+            sort_or_queue(s_z + s_off[l], s_off[l + 1] - s_off[l], c0 + l, m, long_count, long_cells);
+        __syncthreads();
+        for (int32_t i = tid; i < nb; i += kThreads) zs[z0 + i] = s_z[i];
+    } else {
+        for (int32_t i = tid; i < staged; i += kThreads) {
+            const int l = bl[z0 + i];
+            zs[z0 + s_off[l] + atomicAdd(&s_cur[l], 1)] = bz[z0 + i];
+        }
+        __syncthreads();
+        for (int l = tid; l < ncell; l += kThreads)
+            sort_or_queue(zs + z0 + s_off[l], s_off[l + 1] - s_off[l], c0 + l, m, long_count,
+                          long_cells);
+    }
 }
 
 // Bitonic network over 32 * EPL heights held by one warp: element e * 32 +
@@ -733,7 +845,10 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     const int64_t m = (int64_t)g.W * g.H;
     const GridDev gd = grid_dev(g);
     const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
-    cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int32_t) * m, s);
+    // the cell counts, bucket cursors and long-segment counts lie back to back
+    cudaError_t e = cudaMemsetAsync(ws.cnt, 0,
+                                    reinterpret_cast<char *>(ws.long_count + 2) -
+                                        reinterpret_cast<char *>(ws.cnt), s);
     if (e != cudaSuccess) return e;
     k_partition_init<<<1, 32, 0, s>>>(ws.zkeys, stats, n, g.n_slices);
     const int64_t work = vec ? n / 4 + 1 : n;
@@ -745,16 +860,19 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
     k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
     k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
-    if (n > 0)
-        k_scatter<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
-                                                                   ws.start, ws.zs);
-    cudaMemsetAsync(ws.long_count, 0, 2 * sizeof(int32_t), s);
-    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        ws.start, m, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch, ws.long_count,
-                                                        ws.long_cells, m);
-    count_launches(n > 0 ? 10 : 8);
+    if (n > 0) {
+        k_bucket<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
+                                                                  ws.start, ws.bcur, ws.scratch,
+                                                                  ws.bucket_l, ws.zs);
+        k_bucket_sort<<<(unsigned)n_buckets(m), kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch,
+                                                                  ws.bucket_l, ws.zs, ws.long_count,
+                                                                  ws.long_cells);
+        k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count,
+                                                        ws.long_cells);
+        k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                            ws.long_count, ws.long_cells, m);
+    }
+    count_launches(n > 0 ? 10 : 5);
     return cudaGetLastError();
 }
 
@@ -780,9 +898,11 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
     }
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int64_t m = total_cells;
-    cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int32_t) * m, s);
+    cudaError_t e = cudaMemsetAsync(ws.cnt, 0,
+                                    reinterpret_cast<char *>(ws.long_count + 2) -
+                                        reinterpret_cast<char *>(ws.cnt), s);
     if (e != cudaSuccess) return e;
-    int launches = 6;
+    int launches = 5;   // three scan kernels, the two long-segment sorts
     if (blocks > 0) {
         k_count_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt);
         ++launches;
@@ -792,12 +912,13 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
     k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
     k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
     if (blocks > 0) {
-        k_scatter_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.zs);
-        ++launches;
+        k_bucket_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.bcur,
+                                                               ws.scratch, ws.bucket_l, ws.zs);
+        k_bucket_sort<<<(unsigned)n_buckets(m), kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch,
+                                                                  ws.bucket_l, ws.zs, ws.long_count,
+                                                                  ws.long_cells);
+        launches += 2;
     }
-    cudaMemsetAsync(ws.long_count, 0, 2 * sizeof(int32_t), s);
-    k_sort_cells<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        ws.start, m, ws.zs, ws.long_count, ws.long_cells);
     k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);
     k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch, ws.long_count,
                                                         ws.long_cells, m);

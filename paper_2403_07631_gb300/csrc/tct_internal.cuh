@@ -35,7 +35,10 @@ struct Workspace {
     int32_t *start;     // [HW+1] exclusive prefix of cnt
     int32_t *partial;   // [n_scan_blocks + 1]
     float *zs;          // [P]    point heights grouped by cell, sorted per cell
-    float *scratch;     // [P]    copy of very long segments while they are sorted
+    float *scratch;     // [P]    heights by bucket before the bucket sort; later the
+                        //        copy of very long segments while they are sorted
+    uint16_t *bucket_l; // [P]    each bucketed height's cell within its bucket
+    int32_t *bcur;      // [HW / kBucket + 1] fill level of each bucket (zero between builds)
     int32_t *long_count;  // [2]  cells queued for the warp sort, for the block sort
     int32_t *long_cells;  // [HW] their indices (warp sort from the front, block sort from the back)
     int32_t *zkeys;     // [2]    ordered-int min / max z of the finite points
@@ -47,6 +50,9 @@ struct Workspace {
 };
 
 constexpr int kScanTile = 4096;   // cells per scan block
+constexpr int kBucketLog = 10;
+constexpr int kBucket = 1 << kBucketLog;   // cells per bucket of the partition
+inline int64_t n_buckets(int64_t cells) { return (cells + kBucket - 1) / kBucket; }
 
 Workspace carve(void *base, const tct_grid &g, int64_t n_points);
 
