@@ -4,7 +4,7 @@
 //   count    one pass over the points: rasterise, per-cell histogram with
 //            L2 atomics, bounds of z (block-reduced ordered-int atomics),
 //            dropped / non-finite counts;
-//   scan     exclusive prefix of the histogram (three small kernels);
+//   scan     exclusive prefix of the histogram (two small kernels);
 //   bucket   second pass over the points: each z, with its cell's place in
 //            its bucket of kBucket consecutive cells, is appended to the
 //            bucket's range of a staging array (the range of zs the bucket's
@@ -304,9 +304,16 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
         q1 = p1 / 4;
         if (q1 < q0) q1 = q0;
     }
-    for (int64_t q = q0 + tid; q < q1; q += nthreads) {
-        float p[4][3];
-        load4(xyz, stride, q, p);
+    // two groups of four points a thread per round, their loads issued together
+    for (int64_t qq = q0 + tid; qq < q1; qq += 2 * nthreads) {
+        float pp[2][4][3];
+        load4(xyz, stride, qq, pp[0]);
+        const bool two = qq + nthreads < q1;
+        if (two) load4(xyz, stride, qq + nthreads, pp[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        float (&p)[4][3] = pp[h];
         if (kBucketPass) {
             int64_t gc[4];
             float zz[4];
@@ -320,6 +327,7 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) one(p[u][0], p[u][1], p[u][2]);
+        }
         }
     }
     const int64_t a1 = vec ? min(4 * q0, p1) : p1;
@@ -430,48 +438,32 @@ k_scan_reduce(const int32_t *__restrict__ cnt, int64_t m, int32_t *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(1024)
-k_scan_partials(int32_t *partial, int nb) {
-    // one block; each thread owns a contiguous run of the block sums
-    __shared__ int32_t ws[32];
-    const int per = (nb + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    int32_t s = 0;
-    for (int q = 0; q < per; ++q)
-        if (lo + q < nb) s += partial[lo + q];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int32_t w = ws[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        ws[lane] = w;
-    }
-    __syncthreads();
-    int32_t run = x - s + (warp > 0 ? ws[warp - 1] : 0);
-    for (int q = 0; q < per; ++q) {
-        if (lo + q < nb) {
-            const int32_t v = partial[lo + q];
-            partial[lo + q] = run;
-            run += v;
-        }
-    }
-    if (threadIdx.x == 1023) partial[nb] = run;
-}
-
+// The down sweep: each block adds up the sums of the blocks before it (its
+// threads each take a strided share of them), scans its own cells and writes
+// their starts; the last block writes the total.  Block 0 also turns the z
+// bounds of the count pass into the statistics' floats (zkeys and stats may
+// be NULL).
 __global__ void __launch_bounds__(kThreads)
 k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restrict__ partial,
-            int32_t *__restrict__ start, int nb) {
+            int32_t *__restrict__ start, int nb, const int32_t *zkeys, tct_stats *stats) {
+    __shared__ int32_t ws[kThreads / 32];
+    __shared__ int32_t s_pre;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) pre += partial[b];
+    pre = __reduce_add_sync(0xffffffffu, pre);
+    if (lane == 0) ws[warp] = pre;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        s_pre = t;
+        if (blockIdx.x == 0 && zkeys && stats) {
+            stats->z_min = key_float(zkeys[0]);
+            stats->z_max = key_float(zkeys[1]);
+        }
+    }
+    __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kPerThread;
     int32_t v[kPerThread];
     int32_t s = 0;
@@ -480,8 +472,6 @@ k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restric
         v[q] = base + q < m ? cnt[base + q] : 0;
         s += v[q];
     }
-    __shared__ int32_t ws[kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -490,14 +480,14 @@ k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restric
     }
     if (lane == 31) ws[warp] = x;
     __syncthreads();
-    int32_t off = partial[blockIdx.x] + x - s;
+    int32_t off = s_pre + x - s;
     for (int w = 0; w < warp; ++w) off += ws[w];
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
         if (base + q < m) start[base + q] = off;
         off += v[q];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) start[m] = partial[nb];
+    if (blockIdx.x == nb - 1 && threadIdx.x == kThreads - 1) start[m] = off;
 }
 
 // Sort each cell's segment ascending.  Segments of up to 16 heights are
@@ -781,12 +771,6 @@ __global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, in
     }
 }
 
-__global__ void k_partition_finish(const int32_t *zkeys, tct_stats *stats) {
-    if (threadIdx.x == 0) {
-        stats->z_min = key_float(zkeys[0]);
-        stats->z_max = key_float(zkeys[1]);
-    }
-}
 
 // tct_build alone: thread per cell walks the slices with the monotone pointer.
 __global__ void __launch_bounds__(kThreads)
@@ -855,11 +839,9 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     if (n > 0)
         k_count<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                  ws.zkeys, stats);
-    k_partition_finish<<<1, 32, 0, s>>>(ws.zkeys, stats);
     const int nb = (int)((m + kScanTile - 1) / kScanTile);
     k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
-    k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
-    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
+    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, ws.zkeys, stats);
     if (n > 0) {
         k_bucket<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                   ws.start, ws.bcur, ws.scratch,
@@ -872,7 +854,7 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
         k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
                                                             ws.long_count, ws.long_cells, m);
     }
-    count_launches(n > 0 ? 10 : 5);
+    count_launches(n > 0 ? 8 : 3);
     return cudaGetLastError();
 }
 
@@ -902,15 +884,14 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
                                     reinterpret_cast<char *>(ws.long_count + 2) -
                                         reinterpret_cast<char *>(ws.cnt), s);
     if (e != cudaSuccess) return e;
-    int launches = 5;   // three scan kernels, the two long-segment sorts
+    int launches = 4;   // two scan kernels, the two long-segment sorts
     if (blocks > 0) {
         k_count_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt);
         ++launches;
     }
     const int nb = (int)((m + kScanTile - 1) / kScanTile);
     k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
-    k_scan_partials<<<1, 1024, 0, s>>>(ws.partial, nb);
-    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb);
+    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, nullptr, nullptr);
     if (blocks > 0) {
         k_bucket_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.bcur,
                                                                ws.scratch, ws.bucket_l, ws.zs);
