@@ -35,9 +35,9 @@ void tile_dims(int tile, int *TW, int *TH) {
 // Resident CTAs per SM of an instance (the estimate its launch bounds use).
 template <int RK, int RP>
 int resident(int tile) {
-    if (tile == TCT_TILE_32) return inc::Occupancy<RK, RP, 32, 32>::value;
-    if (tile == TCT_TILE_64x56) return inc::Occupancy<RK, RP, 64, 56>::value;
-    return inc::Occupancy<RK, RP, 64, 64>::value;
+    if (tile == TCT_TILE_32) return inc::Occupancy<RK, RP, 32, 32, inc::kStripSmall>::value;
+    if (tile == TCT_TILE_64x56) return inc::Occupancy<RK, RP, 64, 56, 8>::value;
+    return inc::Occupancy<RK, RP, 64, 64, 8>::value;
 }
 
 int resident_for(const EvalConsts &c, int tile) {

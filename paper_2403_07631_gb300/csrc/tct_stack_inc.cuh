@@ -5,7 +5,8 @@
 // radii and organised around one observation: consecutive tomogram slices
 // differ only where the plane passed a point (the redundancy Sec. III-C
 // removes afterwards).  The CTA keeps, in shared memory, the state of every
-// stage for its tile (64 x 64, 64 x 56 or 32 x 32 cells) and the halo and,
+// stage for its tile (64 x 64 or 64 x 56 cells with strips of 8 rows, or
+// 32 x 32 cells with strips of 2 rows for small maps) and the halo and,
 // slice after slice,
 //   1. lists the cells whose next height the plane passed and advances their
 //      pointers into the sorted z segments, the list spread over all threads;
@@ -16,7 +17,7 @@
 //   3. recomputes c^init (Eq. 1, 3-5) only in the row blocks where one of its
 //      inputs changed (listed the same way), marking the cells whose value
 //      changed;
-//   4. re-inflates (Eq. 6) a warp's 32 x 8 strip only when a c^init in its
+//   4. re-inflates (Eq. 6) a warp's 32-column strip only when a c^init in its
 //      window changed, otherwise keeps the previous c^T (bit-identical
 //      inputs give bit-identical results; when few strips changed, their
 //      halves are spread over all warps), and accumulates the uniqueness
@@ -35,15 +36,16 @@
 namespace tct {
 namespace inc {
 
-constexpr int kStrip = 8;             // rows of a thread's inflation strip
 constexpr uint32_t kSat = 0xffffu;   // saturated 16-bit pointer offset
 
-// Tile of TW x TH cells: TW/32 column halves x TH/8 strips, one warp each.
-template <int RK, int RP, int TW, int TH>
+// Tile of TW x TH cells: TW/32 column halves x TH/KS strips of 32 x KS
+// cells, one warp each (a thread holds KS cells of one column).
+template <int RK, int RP, int TW, int TH, int KS>
 struct Geo {
-    static_assert(TW % 32 == 0 && TH % kStrip == 0, "tile made of 32 x 8 strips");
+    static_assert(TW % 32 == 0 && TH % KS == 0 && KS % 2 == 0 && KS <= 8, "tile made of 32 x KS strips");
     static constexpr int NHALF = TW / 32;
-    static constexpr int NW = NHALF * (TH / kStrip);
+    static constexpr int NW = NHALF * (TH / KS);
+    static_assert(NW <= 32, "one bit per warp in the inflation mask");
     static constexpr int NT = 32 * NW;
     static constexpr int HE = RK + RP + 1;
     static constexpr int EW = TW + 2 * HE, EH = TH + 2 * HE;      // elevation region
@@ -148,10 +150,11 @@ struct IncMap {
 // One tile (TW x TH cells at tx0, ty0) of one map over all its slices, by
 // one CTA of Geo::NT threads.  smem is the dynamic buffer of smem_bytes();
 // the caller synchronises before the buffer is used for another tile.
-template <int RK, int RP, int TW, int TH>
+template <int RK, int RP, int TW, int TH, int KS>
 __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c, int tx0, int ty0,
                                            unsigned char *smem, SliceCounters &counters) {
-    using G = Geo<RK, RP, TW, TH>;
+    using G = Geo<RK, RP, TW, TH, KS>;
+    constexpr int kStrip = KS;             // rows of a thread's inflation strip
     constexpr int kNT = G::NT, kNW = G::NW;
     int32_t *s_upre = counters.upre, *s_valid = counters.valid, *s_trav = counters.trav;
 
@@ -703,9 +706,9 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
 
 // Resident CTAs per SM that the tile's shared memory and 64 registers per
 // thread allow.
-template <int RK, int RP, int TW, int TH>
+template <int RK, int RP, int TW, int TH, int KS>
 struct Occupancy {
-    using G = Geo<RK, RP, TW, TH>;
+    using G = Geo<RK, RP, TW, TH, KS>;
     // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA,
     // plus the CTA's static shared memory
     static constexpr int by_smem =
@@ -730,8 +733,8 @@ struct BatchArgs {
     IncMap maps[TCT_MAX_BATCH];
 };
 
-template <int RK, int RP, int TW, int TH>
-__global__ void __launch_bounds__(Geo<RK, RP, TW, TH>::NT, (Occupancy<RK, RP, TW, TH>::value))
+template <int RK, int RP, int TW, int TH, int KS>
+__global__ void __launch_bounds__(Geo<RK, RP, TW, TH, KS>::NT, (Occupancy<RK, RP, TW, TH, KS>::value))
 k_stack_batched(const __grid_constant__ BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SliceCounters counters;
@@ -746,16 +749,16 @@ k_stack_batched(const __grid_constant__ BatchArgs b) {
         while (m + 1 < b.n_maps && b.item_start[m + 1] <= item) ++m;
         const int t = item - b.item_start[m];
         const int tx = t % b.tiles_x[m], ty = t / b.tiles_x[m];
-        stack_tile<RK, RP, TW, TH>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
+        stack_tile<RK, RP, TW, TH, KS>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
         __syncthreads();
     }
 }
 
-template <int RK, int RP, int TW, int TH>
+template <int RK, int RP, int TW, int TH, int KS>
 cudaError_t run_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
-    using G = Geo<RK, RP, TW, TH>;
+    using G = Geo<RK, RP, TW, TH, KS>;
     const size_t smem = G::smem_bytes();
-    auto fn = k_stack_batched<RK, RP, TW, TH>;
+    auto fn = k_stack_batched<RK, RP, TW, TH, KS>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148, fit = 1;
@@ -772,12 +775,17 @@ cudaError_t run_batched(const BatchArgs &b, int ctas_per_sm, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Strip height of the 32 x 32 tile, the shape of small maps: two rows a
+// thread, 16 warps, so that the few CTAs of a small map finish each slice's
+// steps in fewer rounds.
+constexpr int kStripSmall = 2;
+
 // Launch of one (R_K, R_p) instance; defined in the tct_stack_inc_r*.cu units.
 template <int RK, int RP>
 cudaError_t run_radius(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t s) {
-    if (tile == TCT_TILE_32) return run_batched<RK, RP, 32, 32>(b, ctas_per_sm, s);
-    if (tile == TCT_TILE_64x56) return run_batched<RK, RP, 64, 56>(b, ctas_per_sm, s);
-    return run_batched<RK, RP, 64, 64>(b, ctas_per_sm, s);
+    if (tile == TCT_TILE_32) return run_batched<RK, RP, 32, 32, kStripSmall>(b, ctas_per_sm, s);
+    if (tile == TCT_TILE_64x56) return run_batched<RK, RP, 64, 56, 8>(b, ctas_per_sm, s);
+    return run_batched<RK, RP, 64, 64, 8>(b, ctas_per_sm, s);
 }
 
 cudaError_t run_r4(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t s);
