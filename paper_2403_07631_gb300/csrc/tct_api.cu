@@ -24,7 +24,7 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     Layout L;
     size_t o = 0;
     L.cnt = o; o = align_up(o + 4 * m);
-    L.bcur = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_buckets((int64_t)m) : 0));
+    L.bcur = o; o = align_up(o + 4 * (size_t)(n_points > 0 ? n_buckets_max((int64_t)m) : 0));
     L.long_count = o; o = align_up(o + 8);
     L.start = o; o = align_up(o + 4 * (m + 1));
     L.partial = o; o = align_up(o + 4 * (nb + 1));

@@ -35,7 +35,7 @@ BatchLayout batch_layout(const tct_map *maps, int n_maps) {
     const size_t nb = (size_t)((cells + kScanTile - 1) / kScanTile);
     size_t o = 0;
     L.cnt = o; o = align256(o + 4 * (size_t)cells);
-    L.bcur = o; o = align256(o + 4 * (size_t)n_buckets(cells));
+    L.bcur = o; o = align256(o + 4 * (size_t)n_buckets_max(cells));
     L.long_count = o; o = align256(o + 8);
     L.start = o; o = align256(o + 4 * ((size_t)cells + 1));
     L.partial = o; o = align256(o + 4 * (nb + 1));

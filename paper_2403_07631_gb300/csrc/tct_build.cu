@@ -221,7 +221,8 @@ __device__ __forceinline__ void bucket_points(const int64_t (&gc)[U], const floa
                                               const int32_t *__restrict__ start,
                                               int32_t *__restrict__ cnt,
                                               int32_t *__restrict__ bcur, float *__restrict__ bz,
-                                              uint16_t *__restrict__ bl, float *__restrict__ zs) {
+                                              uint16_t *__restrict__ bl, float *__restrict__ zs,
+                                              int blog) {
     const uint32_t act = __activemask();
     const int lane = threadIdx.x & 31;
     uint32_t vm[U];
@@ -237,13 +238,13 @@ __device__ __forceinline__ void bucket_points(const int64_t (&gc)[U], const floa
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (u == first) mine = gc[u];
-    const int64_t b0 = __shfl_sync(act, mine, src) >> kBucketLog;
-    const int32_t pos0 = start[b0 << kBucketLog];        // issued before the atomics
+    const int64_t b0 = __shfl_sync(act, mine, src) >> blog;
+    const int32_t pos0 = start[b0 << blog];              // issued before the atomics
     uint32_t sm[U];
     int n0 = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        sm[u] = __ballot_sync(act, gc[u] >= 0 && (gc[u] >> kBucketLog) == b0);
+        sm[u] = __ballot_sync(act, gc[u] >= 0 && (gc[u] >> blog) == b0);
         n0 += __popc(sm[u]);
     }
     int32_t base = 0;
@@ -263,7 +264,7 @@ __device__ __forceinline__ void bucket_points(const int64_t (&gc)[U], const floa
         if ((sm[u] >> lane) & 1u) {
             const int64_t pos = (int64_t)pos0 + base + run + __popc(sm[u] & lt);
             bz[pos] = z[u];
-            bl[pos] = (uint16_t)(gc[u] & (kBucket - 1));
+            bl[pos] = (uint16_t)(gc[u] & ((1 << blog) - 1));
         } else if (dslot[u] >= 0) {
             zs[dpos[u]] = z[u];
         }
@@ -288,12 +289,12 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
                                             const int32_t *__restrict__ start,
                                             int32_t *__restrict__ bcur, float *__restrict__ bz,
                                             uint16_t *__restrict__ bl, float *__restrict__ zs,
-                                            PointTally &t) {
+                                            int blog, PointTally &t) {
     auto one = [&](float x, float y, float z) {
         if (kBucketPass) {
             const int64_t gc[1] = {finite3(x, y, z) ? point_cell(x, y, g, cell_off) : -1};
             const float zz[1] = {fold_zero(z)};
-            bucket_points<1>(gc, zz, start, cnt, bcur, bz, bl, zs);
+            bucket_points<1>(gc, zz, start, cnt, bcur, bz, bl, zs, blog);
         } else {
             count_point(x, y, z, g, cell_off, cnt, t);
         }
@@ -323,7 +324,7 @@ __device__ __forceinline__ void visit_range(const float *__restrict__ xyz, int s
                                                             : -1;
                 zz[u] = fold_zero(p[u][2]);
             }
-            bucket_points<4>(gc, zz, start, cnt, bcur, bz, bl, zs);
+            bucket_points<4>(gc, zz, start, cnt, bcur, bz, bl, zs, blog);
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) one(p[u][0], p[u][1], p[u][2]);
@@ -353,7 +354,7 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
     t.init();
     visit_range<false>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                        (int64_t)gridDim.x * blockDim.x, g, 0, cnt, nullptr, nullptr, nullptr,
-                       nullptr, nullptr, t);
+                       nullptr, nullptr, 0, t);
     flush_tally(t, zkeys, stats, true);
 }
 
@@ -361,11 +362,11 @@ k_count(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev 
 __global__ void __launch_bounds__(kThreads)
 k_bucket(const float *__restrict__ xyz, int64_t n, int stride, bool vec, GridDev g,
          int32_t *__restrict__ cnt, const int32_t *__restrict__ start, int32_t *__restrict__ bcur,
-         float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs) {
+         float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs, int blog) {
     PointTally t;
     t.init();
     visit_range<true>(xyz, stride, vec, 0, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                      (int64_t)gridDim.x * blockDim.x, g, 0, cnt, start, bcur, bz, bl, zs, t);
+                      (int64_t)gridDim.x * blockDim.x, g, 0, cnt, start, bcur, bz, bl, zs, blog, t);
 }
 
 // Both passes over a batch: block b serves one chunk of one map's points.
@@ -400,21 +401,22 @@ k_count_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt)
     PointTally t;
     t.init();
     visit_range<false>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
-                       m.cell_off, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, t);
+                       m.cell_off, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, 0, t);
     flush_tally(t, m.zkeys, m.stats, true);
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_bucket_batched(const __grid_constant__ PointBatch b, int32_t *__restrict__ cnt,
                  const int32_t *__restrict__ start, int32_t *__restrict__ bcur,
-                 float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs) {
+                 float *__restrict__ bz, uint16_t *__restrict__ bl, float *__restrict__ zs,
+                 int blog) {
     const PointMap &m = b.maps[batch_map_of_block(b)];
     const int64_t p0 = (int64_t)((int)blockIdx.x - m.block_start) * b.chunk;
     const int64_t p1 = min(m.n, p0 + b.chunk);
     PointTally t;
     t.init();
     visit_range<true>(m.xyz, m.stride, m.vec != 0, p0, p1, threadIdx.x, blockDim.x, m.g,
-                      m.cell_off, cnt, start, bcur, bz, bl, zs, t);
+                      m.cell_off, cnt, start, bcur, bz, bl, zs, blog, t);
 }
 
 // Exclusive scan of cnt[0, m) into start[0, m], in tiles of kScanTile.
@@ -528,7 +530,7 @@ __device__ __forceinline__ void sort_segment(float *__restrict__ zs, int32_t s, 
         if (i < n) zs[s + i] = v[i];
 }
 
-// Pass 3: one block per bucket of kBucket cells.  The bucket's staged
+// Pass 3: one block per bucket of 2^blog cells.  The bucket's staged
 // heights sit in the staging arrays at the start of the range of zs its
 // cells occupy; the heights written directly already fill the top of their
 // cells' segments in zs.  The block reads the range of zs into shared
@@ -538,61 +540,70 @@ __device__ __forceinline__ void sort_segment(float *__restrict__ zs, int32_t s, 
 // heights the same happens in global memory.  Segments of 17 .. kWarpSort
 // heights are queued for k_sort_long (from the front of long_cells, counted
 // in long_count[0]), longer ones for k_sort_huge (from the back,
-// long_count[1]).
+// long_count[1]); a block takes its places in each queue with one atomic.
 constexpr int kBucketStage = 8192;
 
-__device__ __forceinline__ void sort_or_queue(float *seg, int32_t n, int64_t cell, int64_t m,
-                                              int32_t *__restrict__ long_count,
-                                              int32_t *__restrict__ long_cells) {
-    if (n <= 1) return;
+// Sorts a segment of up to 16 heights in place; returns 0, or 1 for a
+// segment the warp sort takes (17 .. kWarpSort heights), 2 for the block sort.
+__device__ __forceinline__ int sort_short(float *seg, int32_t n) {
+    if (n <= 1) return 0;
     if (n <= 4) sort_segment<4>(seg, 0, n);
     else if (n <= 8) sort_segment<8>(seg, 0, n);
     else if (n <= 16) sort_segment<16>(seg, 0, n);
-    else if (n <= kWarpSort) long_cells[atomicAdd(long_count, 1)] = (int32_t)cell;
-    else long_cells[m - 1 - atomicAdd(long_count + 1, 1)] = (int32_t)cell;
+    else return n <= kWarpSort ? 1 : 2;
+    return 0;
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_bucket_sort(const int32_t *__restrict__ start, int64_t m, const int32_t *__restrict__ bcur,
               const float *__restrict__ bz, const uint16_t *__restrict__ bl,
               float *__restrict__ zs, int32_t *__restrict__ long_count,
-              int32_t *__restrict__ long_cells) {
+              int32_t *__restrict__ long_cells, int blog) {
     __shared__ int32_t s_off[kBucket + 1];
     __shared__ int32_t s_cur[kBucket];
     __shared__ float s_z[kBucketStage];
+    __shared__ uint16_t s_q[kBucket];            // long segments from the front, huge from the back
+    __shared__ int32_t s_n[2], s_base[2];
     const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.x << kBucketLog;
-    const int ncell = (int)min((int64_t)kBucket, m - c0);
+    const int64_t c0 = (int64_t)blockIdx.x << blog;
+    const int ncell = (int)min((int64_t)1 << blog, m - c0);
     const int32_t z0 = start[c0];
     const int32_t staged = bcur[blockIdx.x];
     for (int l = tid; l <= ncell; l += kThreads) s_off[l] = start[c0 + l] - z0;
     for (int l = tid; l < ncell; l += kThreads) s_cur[l] = 0;
+    if (tid < 2) s_n[tid] = 0;
     __syncthreads();
     const int32_t nb = s_off[ncell];
     if (nb == 0) return;
-    if (nb <= kBucketStage) {
+    const bool staged_in_smem = nb <= kBucketStage;
+    float *seg0 = staged_in_smem ? s_z : zs + z0;
+    if (staged_in_smem) {
         if (staged < nb)
             for (int32_t i = tid; i < nb; i += kThreads) s_z[i] = zs[z0 + i];
         __syncthreads();
-        for (int32_t i = tid; i < staged; i += kThreads) {
-            const int l = bl[z0 + i];
-            s_z[s_off[l] + atomicAdd(&s_cur[l], 1)] = bz[z0 + i];
-        }
-        __syncthreads();
-        for (int l = tid; l < ncell; l += kThreads)
-            sort_or_queue(s_z + s_off[l], s_off[l + 1] - s_off[l], c0 + l, m, long_count, long_cells);
-        __syncthreads();
-        for (int32_t i = tid; i < nb; i += kThreads) zs[z0 + i] = s_z[i];
-    } else {
-        for (int32_t i = tid; i < staged; i += kThreads) {
-            const int l = bl[z0 + i];
-            zs[z0 + s_off[l] + atomicAdd(&s_cur[l], 1)] = bz[z0 + i];
-        }
-        __syncthreads();
-        for (int l = tid; l < ncell; l += kThreads)
-            sort_or_queue(zs + z0 + s_off[l], s_off[l + 1] - s_off[l], c0 + l, m, long_count,
-                          long_cells);
     }
+    for (int32_t i = tid; i < staged; i += kThreads) {
+        const int l = bl[z0 + i];
+        seg0[s_off[l] + atomicAdd(&s_cur[l], 1)] = bz[z0 + i];
+    }
+    __syncthreads();
+    for (int l = tid; l < ncell; l += kThreads) {
+        const int cls = sort_short(seg0 + s_off[l], s_off[l + 1] - s_off[l]);
+        if (cls == 1) s_q[atomicAdd(&s_n[0], 1)] = (uint16_t)l;
+        else if (cls == 2) s_q[ncell - 1 - atomicAdd(&s_n[1], 1)] = (uint16_t)l;
+    }
+    __syncthreads();
+    // the block's long segments join the queues with one atomic each
+    if (tid == 0) {
+        s_base[0] = s_n[0] ? atomicAdd(long_count, s_n[0]) : 0;
+        s_base[1] = s_n[1] ? atomicAdd(long_count + 1, s_n[1]) : 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < s_n[0]; i += kThreads) long_cells[s_base[0] + i] = (int32_t)(c0 + s_q[i]);
+    for (int i = tid; i < s_n[1]; i += kThreads)
+        long_cells[m - 1 - (s_base[1] + i)] = (int32_t)(c0 + s_q[ncell - 1 - i]);
+    if (staged_in_smem)
+        for (int32_t i = tid; i < nb; i += kThreads) zs[z0 + i] = s_z[i];
 }
 
 // Bitonic network over 32 * EPL heights held by one warp: element e * 32 +
@@ -843,12 +854,13 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
     k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, ws.zkeys, stats);
     if (n > 0) {
+        const int blog = bucket_log(m, sm_count());
         k_bucket<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                   ws.start, ws.bcur, ws.scratch,
-                                                                  ws.bucket_l, ws.zs);
-        k_bucket_sort<<<(unsigned)n_buckets(m), kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch,
-                                                                  ws.bucket_l, ws.zs, ws.long_count,
-                                                                  ws.long_cells);
+                                                                  ws.bucket_l, ws.zs, blog);
+        const unsigned nbk = (unsigned)((m + (1 << blog) - 1) >> blog);
+        k_bucket_sort<<<nbk, kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch, ws.bucket_l, ws.zs,
+                                               ws.long_count, ws.long_cells, blog);
         k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count,
                                                         ws.long_cells);
         k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
@@ -893,11 +905,13 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
     k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
     k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, nullptr, nullptr);
     if (blocks > 0) {
+        const int blog = bucket_log(m, sm_count());
         k_bucket_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.bcur,
-                                                               ws.scratch, ws.bucket_l, ws.zs);
-        k_bucket_sort<<<(unsigned)n_buckets(m), kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch,
-                                                                  ws.bucket_l, ws.zs, ws.long_count,
-                                                                  ws.long_cells);
+                                                               ws.scratch, ws.bucket_l, ws.zs,
+                                                               blog);
+        const unsigned nbk = (unsigned)((m + (1 << blog) - 1) >> blog);
+        k_bucket_sort<<<nbk, kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch, ws.bucket_l, ws.zs,
+                                               ws.long_count, ws.long_cells, blog);
         launches += 2;
     }
     k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);

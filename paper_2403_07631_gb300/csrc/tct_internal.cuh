@@ -50,9 +50,19 @@ struct Workspace {
 };
 
 constexpr int kScanTile = 4096;   // cells per scan block
-constexpr int kBucketLog = 10;
-constexpr int kBucket = 1 << kBucketLog;   // cells per bucket of the partition
-inline int64_t n_buckets(int64_t cells) { return (cells + kBucket - 1) / kBucket; }
+// Buckets of the partition: 2^bucket_log consecutive cells, 256 .. 1024,
+// the largest that still gives each SM at least four buckets to sort.
+constexpr int kBucketLogMin = 8, kBucketLogMax = 10;
+constexpr int kBucket = 1 << kBucketLogMax;   // the largest bucket
+inline int bucket_log(int64_t cells, int sms) {
+    int lg = kBucketLogMin;
+    while (lg < kBucketLogMax && (cells >> (lg + 1)) >= 4 * (int64_t)sms) ++lg;
+    return lg;
+}
+// Bucket cursors the workspace holds: enough for the smallest buckets.
+inline int64_t n_buckets_max(int64_t cells) {
+    return (cells + (1 << kBucketLogMin) - 1) >> kBucketLogMin;
+}
 
 Workspace carve(void *base, const tct_grid &g, int64_t n_points);
 
