@@ -403,6 +403,63 @@ def e2e_host(dev, sc, grid, params, steps, kept_only):
     return {"ms": a.elapsed_time(b) / steps, "h2d": P * 12, "d2h": moved[0] // steps}
 
 
+def separate_calls(dev, sc, grid, params, steps, ground, ceil):
+    """The construction alone (tct_build, the paper's T_p) and the evaluation
+    alone on the built layers (tct_evaluate, its T_e; Sec. IV-A, Table III),
+    each timed with CUDA events, L2 flushed before every call, with its own
+    roofline: tct_build moves 12 B per point and writes 8 B per slice-cell,
+    tct_evaluate reads those 8 B and writes 5 B per slice-cell."""
+    import torch
+    from paper_2403_07631_gb300 import tct
+    P, N, H, W = len(sc.points), sc.n_slices, sc.H, sc.W
+    pts = torch.from_numpy(sc.points).to(dev)
+    ws_b = torch.empty(tct.tct_workspace_bytes(grid, P), dtype=torch.uint8, device=dev)
+    ws_e = torch.empty(tct.tct_workspace_bytes(grid, 0, params), dtype=torch.uint8, device=dev)
+    g2 = torch.empty_like(ground)
+    c2 = torch.empty_like(ceil)
+    cost2 = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    mask2 = torch.empty(grid.shape, dtype=torch.uint8, device=dev)
+    keep2 = torch.empty(N, dtype=torch.uint8, device=dev)
+    st_b = torch.zeros(tct.STATS_BYTES, dtype=torch.uint8, device=dev)
+    st_e = torch.zeros(tct.STATS_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    egrid = tct.Grid(grid.x0, grid.y0, grid.res, W, H, grid.d_s, N, 0.0, False)
+
+    def build():
+        tct.tct_build(pts, grid, ws_b, g2, c2, st_b)
+
+    def evaluate():
+        tct.tct_evaluate(egrid, params, g2, c2, ws_e, cost2, mask2, keep2, None, st_e)
+
+    def timed(fn, n):
+        out = []
+        for i in range(n + 3):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if i >= 3:
+                out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    t_b = timed(build, steps)
+    t_e = timed(evaluate, steps)
+    peak, _ = measured_peak_gbs()
+    bb = 12 * P + 8 * N * H * W
+    eb = 13 * N * H * W + N
+    same = bool(torch.equal(g2, ground) and torch.equal(c2, ceil))
+    return {"workload": sc.name, "build_ms": t_b, "evaluate_ms": t_e,
+            "build_roofline_frac": bb / (t_b * 1e-3) / 1e9 / peak,
+            "evaluate_roofline_frac": eb / (t_e * 1e-3) / 1e9 / peak,
+            "build_bytes": bb, "evaluate_bytes": eb,
+            "layers_equal_fused": same,
+            "kernels": "tct_build: partition + per-cell elevation walk; "
+                       "tct_evaluate: slice stack on given layers + chain"}
+
+
 def small_map_graph(dev, params, steps):
     """The two-storey building (200k points, 200 x 200 x 12): a map this small
     is launch-bound, so beside the plain call it is timed as a replay of a
@@ -701,6 +758,7 @@ def main():
     # path search, batches, stress) run at N = 1 only; at N > 1 every rank
     # would repeat them on shared host cores
     if world == 1:
+        out["separate"] = separate_calls(dev, sc, grid, params, min(args.steps, 10), ground, ceil)
         out["sampler"] = sampler_paths(dev, grid, params, cost, ground, mask, stats, args.steps)
         out["small_map"] = small_map_graph(dev, params, args.steps)
         if not args.no_planner:

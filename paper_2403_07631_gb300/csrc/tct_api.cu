@@ -15,7 +15,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t cnt, start, partial, zs, scratch, bucket_l, bcur, long_count, long_cells, zkeys, upre, ubits,
-        stats, queue, total;
+        stats, queue, falls, total;
 };
 
 Layout layout(const tct_grid &g, int64_t n_points) {
@@ -37,6 +37,7 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     L.ubits = o; o = align_up(o + 16 * (TCT_MAX_SLICES + 1));
     L.stats = o; o = align_up(o + sizeof(tct_stats));
     L.queue = o; o = align_up(o + 4);
+    L.falls = o; o = align_up(o + 4);
     L.total = o;
     return L;
 }
@@ -99,6 +100,7 @@ Workspace carve(void *base, const tct_grid &g, int64_t n_points) {
     w.ubits = reinterpret_cast<uint32_t *>(b + L.ubits);
     w.stats = reinterpret_cast<tct_stats *>(b + L.stats);
     w.queue = reinterpret_cast<int32_t *>(b + L.queue);
+    w.falls = reinterpret_cast<int32_t *>(b + L.falls);
     w.bytes = L.total;
     return w;
 }
@@ -284,7 +286,8 @@ int tct_evaluate(const tct_grid *grid, const tct_params *params, const float *d_
     mark(1, s);
     if (e == cudaSuccess)
         e = launch_stack(*grid, c, nullptr, nullptr, d_ground, d_ceil, nullptr, nullptr, d_cost,
-                         d_mask, d_aux, ws.upre, ws.ubits, st, s);
+                         d_mask, d_aux, ws.upre, ws.ubits, st, s, TCT_TILE_AUTO, ws.queue,
+                         ws.falls);
     mark(2, s);
     if (e == cudaSuccess) e = launch_chain(grid->n_slices, ws.upre, ws.ubits, params->flags, d_keep, st, s);
     mark(3, s);

@@ -46,6 +46,7 @@ struct Workspace {
     uint32_t *ubits;    // [128][4] per slice: further uniqueness bits
     tct_stats *stats;   // fallback stats block when the caller passes none
     int32_t *queue;     // [1]    tile queue of the persistent slice-stack kernel
+    int32_t *falls;     // [1]    set when a given ground layer falls from a slice to the next
     size_t bytes;
 };
 
@@ -93,6 +94,7 @@ struct StackArgs {
     const int32_t *start;        // per-cell segments (build path)
     const float *zs;
     const float *gin, *cin;      // given layers (evaluate path)
+    int32_t *falls;              // set by the kernel when a given ground falls
     float *ground, *ceil, *cost, *aux;
     uint8_t *mask;
     int32_t *upre;
@@ -124,11 +126,15 @@ cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *gro
 
 // launchers (tct_stack.cu)
 // tile: TCT_TILE_AUTO, TCT_TILE_64 or TCT_TILE_32 (build path only).
+// Given layers (lists NULL) run the incremental kernel too when it supports
+// the radii and no aux output is asked for; queue and falls are then that
+// call's tile queue and falling-ground flag.
 cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
                          const int32_t *zkeys, const float *gin, const float *cin,
                          float *ground, float *ceil, float *cost, uint8_t *mask, float *aux,
                          int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s,
-                         int tile = TCT_TILE_AUTO);
+                         int tile = TCT_TILE_AUTO, int32_t *queue = nullptr,
+                         int32_t *falls = nullptr);
 // The incremental kernel for the build path; returns cudaErrorNotSupported
 // when no instance matches the window radii (the caller then falls back).
 // tile: TCT_TILE_64 or TCT_TILE_32.

@@ -19,6 +19,8 @@
 // set of such p into a (N+1) x N bit matrix U(p, k); the sequential chain of
 // Sec. III-C is then an O(N) walk over U (k_chain).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "tct_internal.cuh"
@@ -349,9 +351,53 @@ __global__ void k_chain(int n_slices, const int32_t *upre, const uint32_t *ubits
     stats->n_kept = kept;
 }
 
-__global__ void k_stack_init(int32_t *upre, uint32_t *ubits, int32_t *queue) {
+// Given layers whose ground falls somewhere from one slice to the next (not
+// a build's): the uniqueness rows of Sec. III-C taken as the equations state
+// them, every earlier slice p tested (Eq. 8 against p, Eq. 9 against k+1)
+// from the given grounds and the evaluated costs, after the rows the slice
+// stack accumulated are cleared.  Both kernels return at once when no
+// ground fell.
+__global__ void k_uniq_clear(const int32_t *falls, int32_t *upre, uint32_t *ubits) {
+    if (!*falls) return;
+    const int i = threadIdx.x;
+    if (i <= TCT_MAX_SLICES) {
+        upre[i] = 0;
+        ubits[4 * i] = ubits[4 * i + 1] = ubits[4 * i + 2] = ubits[4 * i + 3] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_uniq_general(const int32_t *falls, int64_t HW, int N, const float *__restrict__ ground,
+               const float *__restrict__ cost, float c_b, uint32_t *ubits) {
+    if (!*falls) return;
+    __shared__ uint32_t s_bits[4 * (TCT_MAX_SLICES + 1)];
+    for (int i = threadIdx.x; i < 4 * (TCT_MAX_SLICES + 1); i += blockDim.x) s_bits[i] = 0;
+    __syncthreads();
+    for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < HW;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < N; ++k) {
+            const float ck = cost[(int64_t)k * HW + cell];
+            if (!(ck < c_b)) continue;                       // not traversable
+            const float ek = ground[(int64_t)k * HW + cell];
+            if (k + 1 < N && !(ground[(int64_t)(k + 1) * HW + cell] - ek > 0.0f) &&
+                !(ck < cost[(int64_t)(k + 1) * HW + cell]))
+                continue;                                    // Eq. 9 fails
+            atomicOr(&s_bits[4 * k], 1u);                    // row 0: no slice kept yet
+            for (int p = 0; p < k; ++p) {
+                if (ek - ground[(int64_t)p * HW + cell] > 0.0f || ck < cost[(int64_t)p * HW + cell])
+                    atomicOr(&s_bits[4 * k + ((p + 1) >> 5)], 1u << ((p + 1) & 31));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * N; i += blockDim.x)
+        if (s_bits[i]) atomicOr(&ubits[i], s_bits[i]);
+}
+
+__global__ void k_stack_init(int32_t *upre, uint32_t *ubits, int32_t *queue, int32_t *falls) {
     const int i = threadIdx.x;
     if (i == 0 && queue) *queue = 0;
+    if (i == 0 && falls) *falls = 0;
     if (i <= TCT_MAX_SLICES) {
         upre[i] = 0;
         ubits[4 * i] = ubits[4 * i + 1] = ubits[4 * i + 2] = ubits[4 * i + 3] = 0;
@@ -406,7 +452,8 @@ cudaError_t pick_tile(const StackArgs &a, cudaStream_t s) {
 cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
                          const int32_t *zkeys, const float *gin, const float *cin, float *ground,
                          float *ceil, float *cost, uint8_t *mask, float *aux, int32_t *upre,
-                         uint32_t *ubits, tct_stats *stats, cudaStream_t s, int tile) {
+                         uint32_t *ubits, tct_stats *stats, cudaStream_t s, int tile,
+                         int32_t *queue, int32_t *falls) {
     StackArgs a;
     a.W = g.W;
     a.H = g.H;
@@ -428,13 +475,30 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.ubits = ubits;
     a.stats = stats;
     a.c = c;
-    k_stack_init<<<1, 128, 0, s>>>(upre, ubits, lists ? lists->queue : nullptr);
+    a.falls = falls;
+    if (lists) queue = lists->queue;
+    k_stack_init<<<1, 128, 0, s>>>(upre, ubits, queue, lists ? nullptr : falls);
     count_launches(1);
     if (lists) {
         if (tile == TCT_TILE_AUTO && inc_supported(c, a.N)) tile = choose_tile(c, 1, &a, 1);
         const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
         if (e != cudaErrorNotSupported) return e;
         return pick_tile<true, false>(a, s);
+    }
+    if (!aux && queue && falls && inc_supported(c, a.N)) {
+        // given layers on the incremental kernel; the general uniqueness rows
+        // replace its own when a ground fell
+        if (tile == TCT_TILE_AUTO) tile = choose_tile(c, 1, &a, 1);
+        cudaError_t e = launch_stack_inc(a, queue, tile, s);
+        if (e != cudaErrorNotSupported) {
+            if (e != cudaSuccess) return e;
+            const int64_t HW = (int64_t)a.W * a.H;
+            k_uniq_clear<<<1, 128, 0, s>>>(falls, upre, ubits);
+            const int blocks = (int)std::min<int64_t>((HW + 255) / 256, 4096);
+            k_uniq_general<<<blocks, 256, 0, s>>>(falls, HW, a.N, gin, cost, c.c_b, ubits);
+            count_launches(2);
+            return cudaGetLastError();
+        }
     }
     if (aux) return pick_tile<false, true>(a, s);
     return pick_tile<false, false>(a, s);

@@ -11,8 +11,11 @@ using inc::IncMap;
 IncMap inc_map(const StackArgs &a) {
     IncMap m;
     m.W = a.W; m.H = a.H; m.N = a.N;
-    m.d_s = a.d_s; m.z_min = a.z_min; m.zmin_from_data = a.zmin_from_data;
+    m.d_s = a.d_s; m.z_min = a.z_min; m.zmin_from_data = a.zmin_from_data && a.zkeys;
     m.zkeys = a.zkeys; m.start = a.start; m.zs = a.zs;
+    m.gin = a.start ? nullptr : a.gin;
+    m.cin = a.start ? nullptr : a.cin;
+    m.falls = a.falls;
     m.ground = a.ground; m.ceil = a.ceil; m.cost = a.cost; m.mask = a.mask;
     m.upre = a.upre; m.ubits = a.ubits; m.stats = a.stats;
     return m;

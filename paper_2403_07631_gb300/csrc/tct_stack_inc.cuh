@@ -25,7 +25,9 @@
 //      higher cost than the current one,
 // and writes all four layers of every slice.  Work follows the changes,
 // while the writes of every slice's layers (the algorithmic bytes) are
-// always done.
+// always done.  Given layers (tct_evaluate) take the place of step 1: each
+// slice's ground and ceiling of the region are read and compared with the
+// previous slice's, and only cost and mask are written.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -140,6 +142,8 @@ struct IncMap {
     const int32_t *zkeys;        // ordered-int z bounds from the count pass
     const int32_t *start;        // per-cell segments
     const float *zs;
+    const float *gin, *cin;      // given layers instead of segments (evaluate alone)
+    int32_t *falls;              // set when a given ground falls from one slice to the next
     float *ground, *ceil, *cost;
     uint8_t *mask;
     int32_t *upre;
@@ -181,6 +185,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     constexpr uint32_t kGentHi = (1u << (2 * RP)) - 1u;
     constexpr uint32_t kWinHi = (1u << (2 * RK)) - 1u;
 
+    const bool given = a.gin != nullptr;
     if (tid < 3) counters.nlist[tid] = 0;
     if (tid == 0) counters.infl = 0;
     for (int i = tid; i <= TCT_MAX_SLICES; i += kNT) {
@@ -200,7 +205,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             const int r = e / G::EW, s = e - r * G::EW;
             const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
             b[u] = end[u] = 0;
-            if (e < G::NE && i >= 0 && i < a.H && j >= 0 && j < a.W) {
+            if (!given && e < G::NE && i >= 0 && i < a.H && j >= 0 && j < a.W) {
                 const int64_t cell = (int64_t)i * a.W + j;
                 b[u] = a.start[cell];
                 end[u] = a.start[cell + 1];
@@ -333,6 +338,40 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             counters.nwork[0] = counters.nwork[1] = 0;   // read before the last barrier
             counters.nlist[(k + 1) % 3] = 0;
         }
+        int n_pass;
+        if (given) {
+            // given layers: this slice's ground and ceiling of the region,
+            // compared bit for bit with the previous slice's
+            int moved = 0;
+            const float *gk = a.gin + (int64_t)k * HW, *ck = a.cin + (int64_t)k * HW;
+            for (int e = tid; e < G::NE; e += kNT) {
+                const int r = e / G::EW, s = e - r * G::EW;
+                const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
+                float g = -INFINITY, cz = INFINITY;
+                if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
+                    const int64_t cell = (int64_t)i * a.W + j;
+                    g = gk[cell];
+                    cz = ck[cell];
+                }
+                const float g0 = sEG[e], c0 = sZC[e];
+                const bool gch = __float_as_uint(g) != __float_as_uint(g0);
+                const bool cch = __float_as_uint(cz) != __float_as_uint(c0);
+                if (gch || cch) {
+                    moved = 1;
+                    sEG[e] = g;
+                    sZC[e] = cz;
+                    const uint32_t bit = 1u << (s & 31);
+                    if (gch) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
+                    if (cch) atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
+                    // a ground of the tile that falls: the run-based
+                    // uniqueness bits below assume grounds never fall
+                    if (g < g0 && r >= G::HE && r < G::HE + TH && s >= G::HE && s < G::HE + TW)
+                        *a.falls = 1;
+                }
+            }
+            n_pass = __syncthreads_or(moved);
+            if (tid == 0) counters.infl = 0;   // last read before this barrier
+        } else {
         for (int base = 0; base < G::NE / 4; base += kNT) {
             const int e4 = base + tid;
             float4 z = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
@@ -355,16 +394,17 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         }
         __syncthreads();
         if (tid == 0) counters.infl = 0;   // last read before this barrier
+        n_pass = *nlist;
+        }
         // A quiet slice (no plane passed a height of the region) changes no
         // ground, ceiling, gentle flag, c^init or c^T: it only writes the
         // layers again, with no uniqueness bit (Eq. 9 fails against an
         // identical slice) and the counts of the slice before.
-        const int n_pass = *nlist;
         const bool quiet = !first && n_pass == 0;
         // 1b. advance the listed cells, spread evenly over the threads; each
         //     round reads the next four heights of the segment at once, so a
         //     cell that passes n heights waits for ceil(n / 4) loads, not n
-        if (!quiet) {
+        if (!quiet && !given) {
         for (int t = tid; t < n_pass; t += kNT) {
             const int e = sList[t];
             const int r = e / G::EW, s = e - r * G::EW;
@@ -661,15 +701,18 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             // slice (W H <= 2^30); ground and ceiling are still this slice's:
             // the next slice advances them after its first barrier
             const int64_t sl = (int64_t)k * HW;
-            float *gk = a.ground + sl, *zk = a.ceil + sl, *tk = a.cost + sl;
+            float *gk = given ? nullptr : a.ground + sl, *zk = given ? nullptr : a.ceil + sl;
+            float *tk = a.cost + sl;
             uint8_t *mk = a.mask + sl;
             uint32_t o = (uint32_t)(ty0 + tr0) * (uint32_t)a.W + (uint32_t)j_out;
 #pragma unroll
             for (int q = 0; q < kStrip; ++q, o += (uint32_t)a.W) {
                 if ((inmap >> q) & 1u) {
-                    const int e = (tr0 + q + G::HE) * G::EW + ts + G::HE;
-                    __stcs(gk + o, sEG[e]);
-                    __stcs(zk + o, sZC[e]);
+                    if (!given) {
+                        const int e = (tr0 + q + G::HE) * G::EW + ts + G::HE;
+                        __stcs(gk + o, sEG[e]);
+                        __stcs(zk + o, sZC[e]);
+                    }
                     __stcs(tk + o, cT[q]);
                     mk[o] = (travbits >> q) & 1u;
                 }

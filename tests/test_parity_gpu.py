@@ -144,6 +144,15 @@ def _evaluate_check(eG, eC, params, res=0.1):
     assert np.all((err <= lim)[ok & fin]), "intermediate values out of tolerance"
     keep_ref, robust = P.oracle.simplify(eG, cT, op["c_b"], frag)
     P.assert_keep(g["keep"], eG, g["cost"], dict(keep=keep_ref, robust=robust), params)
+    # without the aux export the call runs the incremental slice stack (for
+    # its window radii) on the given layers: the same checks
+    gi = P.gpu_evaluate(eG, eC, grid, params, aux=False)
+    P.assert_costs(gi["cost"], cT, frag)
+    P.assert_masks(gi["mask"], mask, frag)
+    P.assert_keep(gi["keep"], eG, gi["cost"], dict(keep=keep_ref, robust=robust), params)
+    st = gi["stats"]
+    np.testing.assert_array_equal(np.array(st.valid_cells[:N]), (eG > -np.inf).reshape(N, -1).sum(1))
+    np.testing.assert_array_equal(np.array(st.trav_cells[:N]), gi["mask"].reshape(N, -1).sum(1))
     return g, cT, frag
 
 
@@ -207,6 +216,18 @@ def test_evaluate_nonmonotone_layers_simplification():
 
 
 # --------------------------------------------------------- fused build + evaluate
+
+def test_evaluate_built_layers_equals_fused():
+    # tct_evaluate on the layers tct_build_evaluate wrote gives exactly its
+    # costs, masks and kept slices (one kernel, given layers for segments)
+    sc = scenes.building(16, 90_000, side_cells=110, floors=[0.0, 2.4], ceilings=[2.2, 4.6])
+    grid = _grid_of(sc, n_slices=11)
+    f = P.gpu_build_evaluate(sc.points, grid, PARAMS_ROBOT)
+    eg = tct.Grid(grid.x0, grid.y0, grid.res, grid.W, grid.H, grid.d_s, grid.n_slices, 0.0, False)
+    g = P.gpu_evaluate(f["ground"], f["ceil"], eg, PARAMS_ROBOT, aux=False)
+    for key in ("cost", "mask", "keep"):
+        np.testing.assert_array_equal(g[key], f[key], err_msg=key)
+
 
 def test_two_storey_building_full():
     sc = scenes.two_storey_building()
