@@ -90,8 +90,11 @@ def algorithmic_bytes(P, N, H, W):
 
 
 def stack_bytes(P, N, H, W):
-    # the slice-stack kernel: its outputs, each point's z once, the cell offsets
-    return 13 * N * H * W + 4 * P + 4 * (H * W + 1)
+    # the slice-stack kernel's algorithmic bytes: the per-slice-cell figure of
+    # the path (e^G, e^C, c^T float32 and the mask byte written, 13 B) times
+    # the slice-cells one launch produces; the point heights it reads back
+    # belong to the partition's 12 B per point and are not counted again
+    return 13 * N * H * W
 
 
 class ClockSampler:
@@ -403,6 +406,51 @@ def e2e_host(dev, sc, grid, params, steps, kept_only):
     return {"ms": a.elapsed_time(b) / steps, "h2d": P * 12, "d2h": moved[0] // steps}
 
 
+def host_link(dev, nbytes=256 << 20, reps=5):
+    """The host link as the copy engines see it, in the same run: pinned host
+    to device, device to pinned host, and both at once on two streams (best of
+    `reps` copies of `nbytes`, CUDA events)."""
+    import torch
+    h_src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_dst = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def best(fn):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s1.wait_event(a)
+            s2.wait_event(a)
+            fn()
+            torch.cuda.current_stream().wait_stream(s1)
+            torch.cuda.current_stream().wait_stream(s2)
+            b.record()
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return min(out)
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_src, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h_dst.copy_(d_b, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    t1, t2, t3 = best(h2d), best(d2h), best(both)
+    return {"h2d_gbs": nbytes / (t1 * 1e-3) / 1e9, "d2h_gbs": nbytes / (t2 * 1e-3) / 1e9,
+            "both_gbs": 2 * nbytes / (t3 * 1e-3) / 1e9, "bytes_per_copy": nbytes,
+            "how": "pinned host buffers, cudaMemcpyAsync through torch copies, best of %d" % reps}
+
+
 def separate_calls(dev, sc, grid, params, steps, ground, ceil):
     """The construction alone (tct_build, the paper's T_p) and the evaluation
     alone on the built layers (tct_evaluate, its T_e; Sec. IV-A, Table III),
@@ -711,6 +759,7 @@ def main():
     # so that one map's copies overlap the next map's upload and compute
     e2e = e2e_host(dev, sc, grid, params, args.steps, kept_only=False)
     e2e_kept = e2e_host(dev, sc, grid, params, args.steps, kept_only=True)
+    link = host_link(dev)
 
     st = tct.stats_from(stats)
     peak, peak_src = measured_peak_gbs()
@@ -729,7 +778,8 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
                           "peak_source": peak_src},
-        "roofline": {"kernel": "k_stack_batched<5,2> (per-tile incremental slice stack)", "bound": "hbm",
+        "roofline": {"kernel": "k_stack_batched<5,2,64,56,8> (per-tile incremental slice stack)",
+                     "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
                      "traffic": prof.get("traffic"), "algorithmic_bytes": sb, "ms": stack_ms,
                      "peak_source": peak_src,
@@ -739,7 +789,14 @@ def main():
         "e2e": {"value": units / (e2e["ms"] * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "ms_per_step": e2e["ms"], "api": "tct_build_evaluate_host, all layers",
-                "pipelined": "two streams, two buffer sets"},
+                "pipelined": "two streams, two buffer sets",
+                "host_link": link,
+                # the copies alone at the measured link: the larger direction
+                # when both overlap (two streams), the floor of any host path
+                "link_floor_ms": max(e2e["h2d"] / (link["h2d_gbs"] * 1e9),
+                                     e2e["d2h"] / (link["d2h_gbs"] * 1e9)) * 1e3,
+                "frac_of_link": max(e2e["h2d"] / (link["h2d_gbs"] * 1e9),
+                                    e2e["d2h"] / (link["d2h_gbs"] * 1e9)) * 1e3 / e2e["ms"]},
         "e2e_kept_slices": {"value": units / (e2e_kept["ms"] * 1e-3) / 1e6, "unit": UNIT,
                             "h2d_bytes_per_step": e2e_kept["h2d"],
                             "d2h_bytes_per_step": e2e_kept["d2h"], "ms_per_step": e2e_kept["ms"],

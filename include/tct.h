@@ -299,8 +299,10 @@ size_t tct_workspace_bytes_batched(const tct_map *h_maps, int32_t n_maps,
  * slice stack is one persistent launch that takes (map, tile) items from a
  * queue, largest maps first, and one launch runs every map's chain.  The
  * launch sequence does not depend on the data, so it can be captured into a
- * CUDA graph and replayed.  All maps share r_g and the robot parameters;
- * window radii without a specialised kernel give TCT_ERR_UNSUPPORTED.
+ * CUDA graph and replayed.  All maps share the robot parameters; when they
+ * also share r_g and the window radii have a specialised kernel the slice
+ * stack is one persistent launch, otherwise it runs map after map (each with
+ * its own window, the generic kernel where no specialised one exists).
  * tuning may be NULL (defaults).  Each map's outputs are those of
  * tct_build_evaluate on that map alone.
  */

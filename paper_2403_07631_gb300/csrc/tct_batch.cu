@@ -121,7 +121,6 @@ int check_batch(const tct_map *maps, int n_maps, const tct_params *params, EvalC
         if (m.grid.n_slices > TCT_MAX_SLICES) return TCT_ERR_UNSUPPORTED;
         if ((m.stride != 3 && m.stride != 4) || (m.n > 0 && !m.d_xyz)) return TCT_ERR_INVALID_ARG;
         if (!m.d_ground || !m.d_ceil || !m.d_cost || !m.d_mask || !m.d_keep) return TCT_ERR_INVALID_ARG;
-        if (m.grid.res != maps[0].grid.res) return TCT_ERR_UNSUPPORTED;   // one window for all
         cells += (int64_t)m.grid.W * m.grid.H;
         points += m.n;
     }
@@ -130,7 +129,6 @@ int check_batch(const tct_map *maps, int n_maps, const tct_params *params, EvalC
         const int rc = make_eval_consts(maps[i].grid, *params, c);
         if (rc != TCT_OK) return rc;
     }
-    if (!inc_supported(*c, 0)) return TCT_ERR_UNSUPPORTED;
     return TCT_OK;
 }
 
@@ -210,10 +208,35 @@ int run_batch(const tct_map *maps, int n_maps, const tct_params *params, const t
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_partition_batched(pin.data(), n_maps, tn.points_per_block, L.cells, ws, s);
+    // one persistent launch when every map shares the window (one r_g) and an
+    // instance has its radii; otherwise map after map, each with its own
+    // constants, on the incremental kernel where it has the radii and on the
+    // generic one where not (as the single-map path does)
+    bool shared = true;
+    for (int i = 0; i < n_maps; ++i) {
+        shared = shared && maps[i].grid.res == maps[0].grid.res &&
+                 inc_supported(c, maps[i].grid.n_slices);
+        sorted[i].c = c;
+    }
     int tile = tn.tile;
-    if (tile == TCT_TILE_AUTO) tile = choose_tile(c, n_maps, sorted.data(), 2);
-    if (e == cudaSuccess)
-        e = launch_stack_batched(c, n_maps, sorted.data(), queue, tile, tn.ctas_per_sm, s);
+    if (shared) {
+        if (tile == TCT_TILE_AUTO) tile = choose_tile(c, n_maps, sorted.data(), 2);
+        if (e == cudaSuccess)
+            e = launch_stack_batched(c, n_maps, sorted.data(), queue, tile, tn.ctas_per_sm, s);
+    } else {
+        for (int i = 0; i < n_maps && e == cudaSuccess; ++i) {
+            StackArgs a = sorted[i];
+            const tct_map &m = maps[order[i]];
+            if (make_eval_consts(m.grid, *params, &a.c) != TCT_OK) return TCT_ERR_INVALID_ARG;
+            if (inc_supported(a.c, a.N)) {
+                const int t = tn.tile == TCT_TILE_AUTO ? choose_tile(a.c, 1, &a, 2) : tn.tile;
+                e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+                if (e == cudaSuccess) e = launch_stack_batched(a.c, 1, &a, queue, t, tn.ctas_per_sm, s);
+            } else {
+                e = launch_stack_generic(a, s);
+            }
+        }
+    }
     if (e == cudaSuccess) {
         k_batch_chain<<<n_maps, 128, 0, s>>>(small);
         count_launches(1);

@@ -148,6 +148,9 @@ cudaError_t launch_stack_inc(const StackArgs &a, int32_t *queue, int tile, cudaS
 int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t small_tiles64);
 cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArgs *maps,
                                  int32_t *queue, int tile, int ctas_per_sm, cudaStream_t s);
+// The generic (any window radius) slice stack for one map of the build path;
+// the map's uniqueness rows must be zero and a.c its constants.
+cudaError_t launch_stack_generic(const StackArgs &a, cudaStream_t s);
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits,
                          uint32_t flags, uint8_t *keep, tct_stats *stats, cudaStream_t s);
 

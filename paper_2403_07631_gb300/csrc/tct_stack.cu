@@ -504,6 +504,10 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     return pick_tile<false, false>(a, s);
 }
 
+cudaError_t launch_stack_generic(const StackArgs &a, cudaStream_t s) {
+    return pick_tile<true, false>(a, s);
+}
+
 cudaError_t launch_chain(int n_slices, const int32_t *upre, const uint32_t *ubits, uint32_t flags,
                          uint8_t *keep, tct_stats *stats, cudaStream_t s) {
     k_chain<<<1, 128, 0, s>>>(n_slices, upre, ubits, flags, keep, stats);

@@ -144,11 +144,33 @@ def test_batch_refusals():
                      device="cuda")
     with pytest.raises(tct.TctError, match="workspace"):
         tct.tct_build_evaluate_batched(maps, PARAMS_ROBOT, ws[:1024])
-    other = tct.MapBuffers.allocate(maps[0].xyz, tct.Grid(0.0, 0.0, 0.05, 40, 40, 0.5, 3, 0.0, True))
     with pytest.raises(tct.TctError, match="limit"):
-        tct.tct_build_evaluate_batched([maps[0], other], PARAMS_ROBOT, ws)
-    with pytest.raises(tct.TctError, match="limit"):
-        tct.tct_build_evaluate_batched(maps, dict(PARAMS_ROBOT, patch_radius=3), ws)
+        tct.tct_build_evaluate_batched(maps * 33, PARAMS_ROBOT, ws)      # 66 maps
+
+
+@pytest.mark.parametrize("params", [PARAMS_ROBOT, dict(PARAMS_ROBOT, patch_radius=3)])
+def test_batch_mixed_resolutions_and_generic_radii(params):
+    """Maps at 0.1 m and 0.05 m in one batch (a window each), and a patch
+    radius without a specialised kernel: the batch runs map after map and
+    every map equals the single-map call and the oracle."""
+    scs = _uneven_batch(seed=9, count=2)
+    fine = scenes.building(310, 30_000, 80, 0.05, [0.0, 1.1], [0.9, 2.4], 8.0, 0.01)
+    fine.n_slices = 5
+    scs.append(fine)
+    maps = _maps(scs)
+    ws = torch.empty(tct.tct_workspace_bytes_batched(maps, params), dtype=torch.uint8,
+                     device="cuda")
+    tct.tct_build_evaluate_batched(maps, params, ws)
+    torch.cuda.synchronize()
+    for sc, m in zip(scs, maps):
+        got = _host(m)
+        one = _single(sc, params)
+        for key in ("ground", "ceil", "cost", "mask", "keep"):
+            np.testing.assert_array_equal(got[key], one[key], err_msg=key)
+        ref = P.oracle_all(sc.points, _grid(sc), params)
+        P.assert_costs(got["cost"], ref["cost"], ref["fragile"])
+        P.assert_masks(got["mask"], ref["mask"], ref["fragile"])
+        P.assert_keep(got["keep"], got["ground"], got["cost"], ref, params)
 
 
 @pytest.mark.parametrize("res,params", [(0.1, PARAMS_TABLE1), (0.05, PARAMS_ROBOT)])
