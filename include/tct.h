@@ -63,6 +63,7 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 #define TCT_TILE_64 1                  /* 64 x 64 cells, 512 threads          */
 #define TCT_TILE_32 2                  /* 32 x 32 cells, 128 threads          */
 #define TCT_TILE_64x56 3               /* 64 x 56 cells, 448 threads          */
+#define TCT_TILE_64x40 4               /* 64 x 40 cells, 320 threads          */
 
 /* ---- geometry (Sec. III-A) ---------------------------------------------- */
 #define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (first step of Alg. 1) */

@@ -2,6 +2,8 @@
 // to its compiled window radii; one map is a batch of one.
 #include "tct_stack_inc.cuh"
 
+#include <algorithm>
+
 namespace tct {
 namespace {
 
@@ -32,7 +34,7 @@ cudaError_t dispatch(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t
 // Tile edge lengths of a TCT_TILE_* shape.
 void tile_dims(int tile, int *TW, int *TH) {
     *TW = tile == TCT_TILE_32 ? 32 : 64;
-    *TH = tile == TCT_TILE_32 ? 32 : tile == TCT_TILE_64x56 ? 56 : 64;
+    *TH = tile == TCT_TILE_32 ? 32 : tile == TCT_TILE_64x56 ? 56 : tile == TCT_TILE_64x40 ? 40 : 64;
 }
 
 // Resident CTAs per SM of an instance (the estimate its launch bounds use).
@@ -40,6 +42,7 @@ template <int RK, int RP>
 int resident(int tile) {
     if (tile == TCT_TILE_32) return inc::Occupancy<RK, RP, 32, 32, inc::kStripSmall>::value;
     if (tile == TCT_TILE_64x56) return inc::Occupancy<RK, RP, 64, 56, 8>::value;
+    if (tile == TCT_TILE_64x40) return inc::Occupancy<RK, RP, 64, 40, 8>::value;
     return inc::Occupancy<RK, RP, 64, 64, 8>::value;
 }
 
@@ -59,18 +62,28 @@ int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t 
     for (int i = 0; i < n_maps; ++i)
         tiles64 += (int64_t)((maps[i].W + 63) / 64) * ((maps[i].H + 63) / 64);
     if (tiles64 < small_tiles64 * sms) return TCT_TILE_32;   // small maps: more, smaller CTAs
-    // whole waves of resident CTAs times the cells (with halo) a CTA handles
+    // an SM's work over whole waves: waves x resident CTAs x the cells (with
+    // halo) a CTA handles, divided by what co-resident CTAs gain by hiding
+    // each other's barrier and memory waits (measured on the 1000 x 1000
+    // parking structure: a second CTA per SM makes the slice stack 1.25x
+    // faster, a third 1.05x more)
+    static const double kResidentGain[] = {1.0, 1.0, 1.25, 1.31, 1.35};
     const int he = c.rk + c.patch_radius + 1;
     int best = TCT_TILE_64;
     double best_cost = INFINITY;
-    for (int tile : {TCT_TILE_64, TCT_TILE_64x56}) {
+    for (int tile : {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_64x40}) {
         int TW, TH;
         tile_dims(tile, &TW, &TH);
         int64_t tiles = 0;
         for (int i = 0; i < n_maps; ++i)
             tiles += (int64_t)((maps[i].W + TW - 1) / TW) * ((maps[i].H + TH - 1) / TH);
-        const int64_t slots = (int64_t)sms * (resident_for(c, tile) > 0 ? resident_for(c, tile) : 1);
-        const double cost = (double)((tiles + slots - 1) / slots) * (TW + 2 * he) * (TH + 2 * he);
+        const int res = std::max(1, std::min(4, resident_for(c, tile)));
+        const int64_t slots = (int64_t)sms * res;
+        const int64_t waves = (tiles + slots - 1) / slots;
+        // CTAs an SM runs at once in the last (or only) wave
+        const int64_t per_sm = std::min<int64_t>(res, (tiles + sms - 1) / sms);
+        const double cost = (double)waves * per_sm * (TW + 2 * he) * (TH + 2 * he) /
+                            kResidentGain[per_sm];
         if (cost < best_cost) {
             best_cost = cost;
             best = tile;

@@ -828,6 +828,7 @@ template <int RK, int RP>
 cudaError_t run_radius(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t s) {
     if (tile == TCT_TILE_32) return run_batched<RK, RP, 32, 32, kStripSmall>(b, ctas_per_sm, s);
     if (tile == TCT_TILE_64x56) return run_batched<RK, RP, 64, 56, 8>(b, ctas_per_sm, s);
+    if (tile == TCT_TILE_64x40) return run_batched<RK, RP, 64, 40, 8>(b, ctas_per_sm, s);
     return run_batched<RK, RP, 64, 64, 8>(b, ctas_per_sm, s);
 }
 
