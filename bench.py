@@ -614,7 +614,8 @@ def batched_vs_plain(dev, params, steps):
             "batched_mpoints_per_s": P / (t_graph * 1e-3) / 1e6,
             "batched_slice_cells_per_s": SC / (t_graph * 1e-3),
             "path_roofline_frac": (12 * P + 13 * SC) / (t_graph * 1e-3) / 1e9 / measured_peak_gbs()[0],
-            "tuning": {"tile": {1: "64x64", 2: "32x32", 3: "64x56"}.get(tuning.tile, "auto"),
+            "tuning": {"tile": {1: "64x64", 2: "32x32", 3: "64x56", 4: "64x40",
+                                5: "128x56"}.get(tuning.tile, "auto"),
                        "ctas_per_sm": tuning.ctas_per_sm,
                        "points_per_block": tuning.points_per_block}}
 
@@ -779,8 +780,9 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_per_step": algorithmic_bytes(P, N, H, W),
                           "peak_source": peak_src},
-        "roofline": {"kernel": "k_stack_batched (per-tile incremental slice stack; 64 x 56 tiles "
-                               "of 8-row strips on the parking structure)",
+        "roofline": {"kernel": "k_stack_batched (per-tile incremental slice stack; 128 x 56 tiles "
+                               "of 8-row strips, one CTA of 28 warps per SM, on the parking "
+                               "structure)",
                      "bound": "hbm",
                      "achieved": stack_gbs, "peak": peak, "unit": "GB/s", "frac": stack_gbs / peak,
                      "traffic": prof.get("traffic"), "algorithmic_bytes": sb, "ms": stack_ms,

@@ -61,9 +61,10 @@ typedef struct CUstream_st *tct_stream; /* a cudaStream_t */
 /* tile shapes of the slice-stack kernel (tct_tuning.tile) */
 #define TCT_TILE_AUTO 0                /* the shape with the least work per SM over whole waves */
 #define TCT_TILE_64 1                  /* 64 x 64 cells, 512 threads          */
-#define TCT_TILE_32 2                  /* 32 x 32 cells, 128 threads          */
+#define TCT_TILE_32 2                  /* 32 x 32 cells, 512 threads          */
 #define TCT_TILE_64x56 3               /* 64 x 56 cells, 448 threads          */
 #define TCT_TILE_64x40 4               /* 64 x 40 cells, 320 threads          */
+#define TCT_TILE_128x56 5              /* 128 x 56 cells, 896 threads, one CTA per SM */
 
 /* ---- geometry (Sec. III-A) ---------------------------------------------- */
 #define TCT_GRID_ZMIN_FROM_DATA 1u     /* z_min = lowest finite z of the cloud (first step of Alg. 1) */

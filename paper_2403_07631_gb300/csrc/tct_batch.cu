@@ -455,7 +455,7 @@ extern "C" int tct_build_evaluate_batched(const tct_map *h_maps, int32_t n_maps,
     tct_tuning tn = tuning ? *tuning : default_tuning();
     if (tn.points_per_block < 4 || tn.points_per_block % 4) return TCT_ERR_INVALID_ARG;
     if (tn.tile != TCT_TILE_AUTO && tn.tile != TCT_TILE_64 && tn.tile != TCT_TILE_32 &&
-        tn.tile != TCT_TILE_64x56 && tn.tile != TCT_TILE_64x40)
+        tn.tile != TCT_TILE_64x56 && tn.tile != TCT_TILE_64x40 && tn.tile != TCT_TILE_128x56)
         return TCT_ERR_INVALID_ARG;
     return run_batch(h_maps, n_maps, params, tn, c, d_ws, (cudaStream_t)stream);
 }
@@ -472,7 +472,7 @@ extern "C" int tct_autotune_batched(const tct_map *h_maps, int32_t n_maps,
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return TCT_ERR_CUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return TCT_ERR_CUDA; }
-    const int tiles[] = {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_64x40, TCT_TILE_32};
+    const int tiles[] = {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_64x40, TCT_TILE_128x56, TCT_TILE_32};
     const int ctas[] = {0, 1};
     const int ppb[] = {2048, 8192};
     float best = INFINITY;

@@ -125,7 +125,7 @@ cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *gro
                               float *ceil, cudaStream_t s);
 
 // launchers (tct_stack.cu)
-// tile: TCT_TILE_AUTO, TCT_TILE_64 or TCT_TILE_32 (build path only).
+// tile: TCT_TILE_AUTO or one of the TCT_TILE_* shapes.
 // Given layers (lists NULL) run the incremental kernel too when it supports
 // the radii and no aux output is asked for; queue and falls are then that
 // call's tile queue and falling-ground flag.
@@ -137,7 +137,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
                          int32_t *falls = nullptr);
 // The incremental kernel for the build path; returns cudaErrorNotSupported
 // when no instance matches the window radii (the caller then falls back).
-// tile: TCT_TILE_64 or TCT_TILE_32.
+// tile: one of the TCT_TILE_* shapes.
 bool inc_supported(const EvalConsts &c, int n_slices);
 cudaError_t launch_stack_inc(const StackArgs &a, int32_t *queue, int tile, cudaStream_t s);
 // One persistent launch over the tiles of n_maps maps (largest first);

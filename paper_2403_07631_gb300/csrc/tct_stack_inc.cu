@@ -33,8 +33,10 @@ cudaError_t dispatch(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream_t
 
 // Tile edge lengths of a TCT_TILE_* shape.
 void tile_dims(int tile, int *TW, int *TH) {
-    *TW = tile == TCT_TILE_32 ? 32 : 64;
-    *TH = tile == TCT_TILE_32 ? 32 : tile == TCT_TILE_64x56 ? 56 : tile == TCT_TILE_64x40 ? 40 : 64;
+    *TW = tile == TCT_TILE_32 ? 32 : tile == TCT_TILE_128x56 ? 128 : 64;
+    *TH = tile == TCT_TILE_32 ? 32
+        : tile == TCT_TILE_64x56 || tile == TCT_TILE_128x56 ? 56
+        : tile == TCT_TILE_64x40 ? 40 : 64;
 }
 
 // Resident CTAs per SM of an instance (the estimate its launch bounds use).
@@ -43,6 +45,7 @@ int resident(int tile) {
     if (tile == TCT_TILE_32) return inc::Occupancy<RK, RP, 32, 32, inc::kStripSmall>::value;
     if (tile == TCT_TILE_64x56) return inc::Occupancy<RK, RP, 64, 56, 8>::value;
     if (tile == TCT_TILE_64x40) return inc::Occupancy<RK, RP, 64, 40, 8>::value;
+    if (tile == TCT_TILE_128x56) return inc::Occupancy<RK, RP, 128, 56, 8>::value;
     return inc::Occupancy<RK, RP, 64, 64, 8>::value;
 }
 
@@ -68,10 +71,19 @@ int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t 
     // parking structure: a second CTA per SM makes the slice stack 1.25x
     // faster, a third 1.05x more)
     static const double kResidentGain[] = {1.0, 1.0, 1.25, 1.31, 1.35};
+    // One CTA of 28 warps (128 x 56) hides about as much as two of 14 (1.18x
+    // against 1.25x, measured on the same map) and carries less halo per
+    // cell.  Its 896 threads leave 72 registers a thread, fewer than the
+    // window-radius-12 code takes in its other shapes (96 in the 64 x 40
+    // tile), and there it measured slower (4000 x 4000 cave terrain: 12.70
+    // against 12.28 ms for 64 x 40), so it is weighed for the smaller windows only.
+    constexpr double kWideGain = 1.18;
+    const bool wide_ok = c.rk <= 5;
     const int he = c.rk + c.patch_radius + 1;
     int best = TCT_TILE_64;
     double best_cost = INFINITY;
-    for (int tile : {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_64x40}) {
+    for (int tile : {TCT_TILE_64, TCT_TILE_64x56, TCT_TILE_64x40, TCT_TILE_128x56}) {
+        if (tile == TCT_TILE_128x56 && !wide_ok) continue;
         int TW, TH;
         tile_dims(tile, &TW, &TH);
         int64_t tiles = 0;
@@ -82,8 +94,8 @@ int choose_tile(const EvalConsts &c, int n_maps, const StackArgs *maps, int64_t 
         const int64_t waves = (tiles + slots - 1) / slots;
         // CTAs an SM runs at once in the last (or only) wave
         const int64_t per_sm = std::min<int64_t>(res, (tiles + sms - 1) / sms);
-        const double cost = (double)waves * per_sm * (TW + 2 * he) * (TH + 2 * he) /
-                            kResidentGain[per_sm];
+        const double gain = tile == TCT_TILE_128x56 ? kWideGain : kResidentGain[per_sm];
+        const double cost = (double)waves * per_sm * (TW + 2 * he) * (TH + 2 * he) / gain;
         if (cost < best_cost) {
             best_cost = cost;
             best = tile;

@@ -5,8 +5,9 @@
 // radii and organised around one observation: consecutive tomogram slices
 // differ only where the plane passed a point (the redundancy Sec. III-C
 // removes afterwards).  The CTA keeps, in shared memory, the state of every
-// stage for its tile (64 x 64 or 64 x 56 cells with strips of 8 rows, or
-// 32 x 32 cells with strips of 2 rows for small maps) and the halo and,
+// stage for its tile (64 x 64, 64 x 56, 64 x 40 or 128 x 56 cells with strips
+// of 8 rows, or 32 x 32 cells with strips of 2 rows for small maps) and the
+// halo and,
 // slice after slice,
 //   1. lists the cells whose next height the plane passed and advances their
 //      pointers into the sorted z segments, the list spread over all threads;
@@ -829,6 +830,7 @@ cudaError_t run_radius(const BatchArgs &b, int tile, int ctas_per_sm, cudaStream
     if (tile == TCT_TILE_32) return run_batched<RK, RP, 32, 32, kStripSmall>(b, ctas_per_sm, s);
     if (tile == TCT_TILE_64x56) return run_batched<RK, RP, 64, 56, 8>(b, ctas_per_sm, s);
     if (tile == TCT_TILE_64x40) return run_batched<RK, RP, 64, 40, 8>(b, ctas_per_sm, s);
+    if (tile == TCT_TILE_128x56) return run_batched<RK, RP, 128, 56, 8>(b, ctas_per_sm, s);
     return run_batched<RK, RP, 64, 64, 8>(b, ctas_per_sm, s);
 }
 

@@ -55,7 +55,7 @@ class TctStats(ctypes.Structure):
 
 STATS_BYTES = ctypes.sizeof(TctStats)
 MAX_BATCH = 64
-TILE_AUTO, TILE_64, TILE_32, TILE_64x56, TILE_64x40 = 0, 1, 2, 3, 4
+TILE_AUTO, TILE_64, TILE_32, TILE_64x56, TILE_64x40, TILE_128x56 = 0, 1, 2, 3, 4, 5
 
 
 class TctMap(ctypes.Structure):

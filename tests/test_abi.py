@@ -137,6 +137,7 @@ def test_constants_match_the_header(tmp_path):
              "TCT_MAX_BATCH": tct.MAX_BATCH, "TCT_TILE_AUTO": tct.TILE_AUTO,
              "TCT_TILE_64": tct.TILE_64, "TCT_TILE_32": tct.TILE_32,
              "TCT_TILE_64x56": tct.TILE_64x56, "TCT_TILE_64x40": tct.TILE_64x40,
+             "TCT_TILE_128x56": tct.TILE_128x56,
              "TCT_HOST_KEPT_ONLY": tct.HOST_KEPT_ONLY}
     lines = ['#include <stdio.h>', '#include "tct.h"', 'int main(void) {']
     lines += [f'    printf("{k} %lld\\n", (long long)({k}));' for k in pairs]

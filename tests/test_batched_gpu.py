@@ -68,7 +68,7 @@ def _single(sc, params):
 
 @pytest.mark.parametrize("tuning", [None, (tct.TILE_64, 0, 4096), (tct.TILE_32, 1, 2048),
                                     (tct.TILE_64, 1, 8192), (tct.TILE_64x56, 0, 4096),
-                                    (tct.TILE_64x40, 0, 4096)])
+                                    (tct.TILE_64x40, 0, 4096), (tct.TILE_128x56, 0, 4096)])
 def test_batch_matches_oracle_and_single_path(tuning):
     scs = _uneven_batch()
     maps = _maps(scs)
@@ -129,7 +129,7 @@ def test_autotune_then_run():
     ws = torch.empty(tct.tct_workspace_bytes_batched(maps, PARAMS_ROBOT), dtype=torch.uint8,
                      device="cuda")
     t = tct.tct_autotune_batched(maps, PARAMS_ROBOT, ws)
-    assert t.tile in (tct.TILE_64, tct.TILE_32, tct.TILE_64x56, tct.TILE_64x40)
+    assert t.tile in (tct.TILE_64, tct.TILE_32, tct.TILE_64x56, tct.TILE_64x40, tct.TILE_128x56)
     assert t.points_per_block % 4 == 0
     tct.tct_build_evaluate_batched(maps, PARAMS_ROBOT, ws, t)
     torch.cuda.synchronize()
@@ -176,7 +176,8 @@ def test_batch_mixed_resolutions_and_generic_radii(params):
 
 
 @pytest.mark.parametrize("res,params", [(0.1, PARAMS_TABLE1), (0.05, PARAMS_ROBOT)])
-@pytest.mark.parametrize("tile", [tct.TILE_64x56, tct.TILE_64x40, tct.TILE_64, tct.TILE_32])
+@pytest.mark.parametrize("tile", [tct.TILE_64x56, tct.TILE_64x40, tct.TILE_64, tct.TILE_32,
+                                  tct.TILE_128x56])
 def test_batch_other_window_radii(res, params, tile):
     """The radius-4 (Table I, 0.1 m) and radius-12 (0.05 m) instances in every
     tile shape, on maps with ragged last tiles."""
