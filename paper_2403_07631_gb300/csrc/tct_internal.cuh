@@ -51,9 +51,9 @@ struct Workspace {
 };
 
 constexpr int kScanTile = 4096;   // cells per scan block
-// Buckets of the partition: 2^bucket_log consecutive cells, 256 .. 1024,
+// Buckets of the partition: 2^bucket_log consecutive cells, 64 .. 1024,
 // the largest that still gives each SM at least four buckets to sort.
-constexpr int kBucketLogMin = 8, kBucketLogMax = 10;
+constexpr int kBucketLogMin = 6, kBucketLogMax = 10;
 constexpr int kBucket = 1 << kBucketLogMax;   // the largest bucket
 inline int bucket_log(int64_t cells, int sms) {
     int lg = kBucketLogMin;

@@ -617,6 +617,8 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
             // few strips changed: their halves (kStrip / 2 rows each) are
             // spread over the warps, half j on warp j, and handed to the
             // owner through the block list (free until the next slice)
+            // (at most NW / 2 strips' halves of kStrip / 2 rows: TW TH / 2 floats,
+            // within the list's NE >= TW TH 16-bit entries)
             float *slots = reinterpret_cast<float *>(sList);
             if (warp < 2 * ndirty) {
                 uint32_t m = dmask;
