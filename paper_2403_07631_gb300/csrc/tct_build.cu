@@ -492,11 +492,20 @@ k_scan_down(const int32_t *__restrict__ cnt, int64_t m, const int32_t *__restric
     if (blockIdx.x == nb - 1 && threadIdx.x == kThreads - 1) start[m] = off;
 }
 
+// Exclusive scan of ws.cnt[0, m) into ws.start[0, m]; returns the launches.
+int launch_scan(const Workspace &ws, int64_t m, const int32_t *zkeys, tct_stats *stats,
+                cudaStream_t s) {
+    const int nb = (int)((m + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
+    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, zkeys, stats);
+    return 2;
+}
+
 // Sort each cell's segment ascending.  Segments of up to 16 heights are
 // sorted in registers by a bitonic network (padded with +inf); segments of
-// up to kWarpSort heights are queued for k_sort_long (from the front of
-// long_cells, counted in long_count[0]), longer ones for k_sort_huge (from
-// the back, counted in long_count[1]).
+// up to kWarpSort heights are queued for the warp sort of k_sort_queued (from
+// the front of long_cells, counted in long_count[0]), longer ones for its
+// block sort (from the back, counted in long_count[1]).
 constexpr int kWarpSort = 256;
 template <int L>
 __device__ __forceinline__ void bitonic_sort(float (&v)[L]) {
@@ -538,9 +547,10 @@ __device__ __forceinline__ void sort_segment(float *__restrict__ zs, int32_t s, 
 // (shared-memory cursors), sorts segments of up to 16 heights in registers
 // and writes the range back.  When the bucket holds more than kBucketStage
 // heights the same happens in global memory.  Segments of 17 .. kWarpSort
-// heights are queued for k_sort_long (from the front of long_cells, counted
-// in long_count[0]), longer ones for k_sort_huge (from the back,
-// long_count[1]); a block takes its places in each queue with one atomic.
+// heights are queued for the warp sort of k_sort_queued (from the front of
+// long_cells, counted in long_count[0]), longer ones for its block sort (from
+// the back, long_count[1]); a block takes its places in each queue with one
+// atomic.
 constexpr int kBucketStage = 8192;
 
 // Sorts a segment of up to 16 heights in place; returns 0, or 1 for a
@@ -655,23 +665,6 @@ __device__ __forceinline__ void warp_sort_segment(float *__restrict__ zs, int32_
         if (e * 32 + lane < n) zs[s + e * 32 + lane] = v[e];
 }
 
-// One warp per long segment (17 .. kWarpSort heights), sorted in the warp's
-// registers.
-__global__ void __launch_bounds__(kThreads)
-k_sort_long(const int32_t *__restrict__ start, float *__restrict__ zs,
-            const int32_t *__restrict__ long_count, const int32_t *__restrict__ long_cells) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int total = long_count[0];
-    for (int t = blockIdx.x * (kThreads / 32) + wib; t < total; t += gridDim.x * (kThreads / 32)) {
-        const int32_t c = long_cells[t];
-        const int32_t s = start[c], n = start[c + 1] - s;
-        if (n <= 32) warp_sort_segment<1>(zs, s, n, lane);
-        else if (n <= 64) warp_sort_segment<2>(zs, s, n, lane);
-        else if (n <= 128) warp_sort_segment<4>(zs, s, n, lane);
-        else warp_sort_segment<8>(zs, s, n, lane);
-    }
-}
-
 // One block per huge segment (more than kWarpSort heights).  Up to kHugeStage
 // heights are sorted by a bitonic network in shared memory (padded with
 // +inf), a barrier between its steps.  Longer segments (a cloud that puts
@@ -715,10 +708,13 @@ __device__ void block_sort_chunk(float *__restrict__ seg, int32_t n, float *buf)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kHugeThreads)
-k_sort_huge(const int32_t *__restrict__ start, float *__restrict__ zs,
-            float *__restrict__ scratch, const int32_t *__restrict__ long_count,
-            const int32_t *__restrict__ long_cells, int64_t m) {
+// Both queues in one launch: the blocks take the block-sort segments (from
+// the back of long_cells) in turn first, then their warps take the segments of
+// 17 .. kWarpSort heights (from the front), each sorted in a warp's registers.
+__global__ void __launch_bounds__(kHugeThreads, 2)
+k_sort_queued(const int32_t *__restrict__ start, float *__restrict__ zs,
+              float *__restrict__ scratch, const int32_t *__restrict__ long_count,
+              const int32_t *__restrict__ long_cells, int64_t m) {
     __shared__ float buf[kHugeStage];
     const int tid = threadIdx.x;
     const int total = long_count[1];
@@ -763,9 +759,20 @@ k_sort_huge(const int32_t *__restrict__ start, float *__restrict__ zs,
             __syncthreads();
         }
     }
+    const int lane = tid & 31, wib = tid >> 5;
+    constexpr int kWarps = kHugeThreads / 32;
+    const int n_long = long_count[0];
+    for (int t = blockIdx.x * kWarps + wib; t < n_long; t += gridDim.x * kWarps) {
+        const int32_t c = long_cells[t];
+        const int32_t s = start[c], n = start[c + 1] - s;
+        if (n <= 32) warp_sort_segment<1>(zs, s, n, lane);
+        else if (n <= 64) warp_sort_segment<2>(zs, s, n, lane);
+        else if (n <= 128) warp_sort_segment<4>(zs, s, n, lane);
+        else warp_sort_segment<8>(zs, s, n, lane);
+    }
 }
 
-// Blocks of the two long-segment sorts: one resident wave each.
+// Blocks of the long-segment sorts: a resident wave (two blocks per SM).
 int sm_count() {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -850,9 +857,7 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
     if (n > 0)
         k_count<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
                                                                  ws.zkeys, stats);
-    const int nb = (int)((m + kScanTile - 1) / kScanTile);
-    k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
-    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, ws.zkeys, stats);
+    const int scan_launches = launch_scan(ws, m, ws.zkeys, stats, s);
     if (n > 0) {
         const int blog = bucket_log(m, sm_count());
         k_bucket<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,
@@ -861,12 +866,10 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
         const unsigned nbk = (unsigned)((m + (1 << blog) - 1) >> blog);
         k_bucket_sort<<<nbk, kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch, ws.bucket_l, ws.zs,
                                                ws.long_count, ws.long_cells, blog);
-        k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count,
-                                                        ws.long_cells);
-        k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
-                                                            ws.long_count, ws.long_cells, m);
+        k_sort_queued<<<2 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                              ws.long_count, ws.long_cells, m);
     }
-    count_launches(n > 0 ? 8 : 3);
+    count_launches((n > 0 ? 5 : 1) + scan_launches);
     return cudaGetLastError();
 }
 
@@ -896,14 +899,12 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
                                     reinterpret_cast<char *>(ws.long_count + 2) -
                                         reinterpret_cast<char *>(ws.cnt), s);
     if (e != cudaSuccess) return e;
-    int launches = 4;   // two scan kernels, the two long-segment sorts
+    int launches = 1;   // the long-segment sorts
     if (blocks > 0) {
         k_count_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt);
         ++launches;
     }
-    const int nb = (int)((m + kScanTile - 1) / kScanTile);
-    k_scan_reduce<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial);
-    k_scan_down<<<nb, kThreads, 0, s>>>(ws.cnt, m, ws.partial, ws.start, nb, nullptr, nullptr);
+    launches += launch_scan(ws, m, nullptr, nullptr, s);
     if (blocks > 0) {
         const int blog = bucket_log(m, sm_count());
         k_bucket_batched<<<(unsigned)blocks, kThreads, 0, s>>>(b, ws.cnt, ws.start, ws.bcur,
@@ -914,9 +915,8 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
                                                ws.long_count, ws.long_cells, blog);
         launches += 2;
     }
-    k_sort_long<<<8 * sm_count(), kThreads, 0, s>>>(ws.start, ws.zs, ws.long_count, ws.long_cells);
-    k_sort_huge<<<4 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch, ws.long_count,
-                                                        ws.long_cells, m);
+    k_sort_queued<<<2 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+                                                          ws.long_count, ws.long_cells, m);
     count_launches(launches);
     return cudaGetLastError();
 }
