@@ -256,10 +256,9 @@ int tct_build(const float *d_xyz, int64_t n, int32_t stride, const tct_grid *gri
     if (ws_bytes < tct_workspace_bytes(grid, n, nullptr)) return TCT_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
     const Workspace ws = carve(d_ws, *grid, n);
-    tct_stats *st = d_stats ? d_stats : ws.stats;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(tct_stats), s);
+    tct_stats *st = d_stats ? d_stats : ws.stats;    // zeroed by the partition's first launch
     mark(0, s);
-    if (e == cudaSuccess) e = launch_partition(d_xyz, n, stride, *grid, ws, st, s);
+    cudaError_t e = launch_partition(d_xyz, n, stride, *grid, ws, st, s);
     mark(1, s);
     if (e == cudaSuccess) e = launch_elevations(*grid, ws, d_ground, d_ceil, s);
     mark(2, s);
@@ -310,10 +309,9 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
     if (rc != TCT_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const Workspace ws = carve(d_ws, *grid, n);
-    tct_stats *st = d_stats ? d_stats : ws.stats;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(tct_stats), s);
+    tct_stats *st = d_stats ? d_stats : ws.stats;    // zeroed by the partition's first launch
     mark(0, s);
-    if (e == cudaSuccess) e = launch_partition(d_xyz, n, stride, *grid, ws, st, s);
+    cudaError_t e = launch_partition(d_xyz, n, stride, *grid, ws, st, s);
     mark(1, s);
     if (e == cudaSuccess)
         e = launch_stack(*grid, c, &ws, ws.zkeys, nullptr, nullptr, d_ground, d_ceil, d_cost,
