@@ -781,11 +781,17 @@ int sm_count() {
 }
 
 // The statistics block starts from zero (the partition's passes add to it),
-// then takes the call's sizes; the z bounds start empty.
-__global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices) {
+// then takes the call's sizes; the z bounds start empty.  The slice stack's
+// uniqueness rows and tile queue of the same workspace are cleared here too,
+// a launch ahead of their use.
+__global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices,
+                                 int32_t *upre, uint32_t *ubits, int32_t *queue) {
     int32_t *w = reinterpret_cast<int32_t *>(stats);
     for (int i = threadIdx.x; i < (int)(sizeof(tct_stats) / sizeof(int32_t)); i += blockDim.x)
         w[i] = 0;
+    for (int i = threadIdx.x; i <= TCT_MAX_SLICES; i += blockDim.x) upre[i] = 0;
+    for (int i = threadIdx.x; i < 4 * (TCT_MAX_SLICES + 1); i += blockDim.x) ubits[i] = 0;
+    if (threadIdx.x == 0) *queue = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         zkeys[0] = float_key(INFINITY);
@@ -858,7 +864,8 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
                                     reinterpret_cast<char *>(ws.long_count + 2) -
                                         reinterpret_cast<char *>(ws.cnt), s);
     if (e != cudaSuccess) return e;
-    k_partition_init<<<1, 256, 0, s>>>(ws.zkeys, stats, n, g.n_slices);
+    k_partition_init<<<1, 256, 0, s>>>(ws.zkeys, stats, n, g.n_slices, ws.upre, ws.ubits,
+                                       ws.queue);
     const int64_t work = vec ? n / 4 + 1 : n;
     if (n > 0)
         k_count<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(xyz, n, stride, vec, gd, ws.cnt,

@@ -126,6 +126,8 @@ cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *gro
 
 // launchers (tct_stack.cu)
 // tile: TCT_TILE_AUTO or one of the TCT_TILE_* shapes.
+// lists: the workspace launch_partition has just filled (its first launch
+// also cleared that workspace's uniqueness rows and tile queue).
 // Given layers (lists NULL) run the incremental kernel too when it supports
 // the radii and no aux output is asked for; queue and falls are then that
 // call's tile queue and falling-ground flag.

@@ -476,15 +476,15 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.stats = stats;
     a.c = c;
     a.falls = falls;
-    if (lists) queue = lists->queue;
-    k_stack_init<<<1, 128, 0, s>>>(upre, ubits, queue, lists ? nullptr : falls);
-    count_launches(1);
     if (lists) {
+        // the partition of this workspace has cleared its uniqueness rows and queue
         if (tile == TCT_TILE_AUTO && inc_supported(c, a.N)) tile = choose_tile(c, 1, &a, 1);
         const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
         if (e != cudaErrorNotSupported) return e;
         return pick_tile<true, false>(a, s);
     }
+    k_stack_init<<<1, 128, 0, s>>>(upre, ubits, queue, falls);
+    count_launches(1);
     if (!aux && queue && falls && inc_supported(c, a.N)) {
         // given layers on the incremental kernel; the general uniqueness rows
         // replace its own when a ground fell
