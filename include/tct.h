@@ -428,11 +428,13 @@ int tct_plan_paths(tct_planner *planner, int32_t n_queries, const int32_t *h_sta
 /* ---- profiling --------------------------------------------------------- */
 
 /*
- * Turns per-phase timing on (on != 0) or off for the following calls on the
- * calling thread's current device.  While on, tct_build, tct_evaluate and
+ * Turns per-phase timing on (on != 0) or off for the following calls made by
+ * the calling thread.  While on, tct_build, tct_evaluate and
  * tct_build_evaluate record CUDA events on their stream around each phase
  * (Sec. IV-A times construction and evaluation separately in the same way).
- * The events are created by the first call that turns timing on.
+ * The events are created by the thread's first call that turns timing on, on
+ * the device then current; calls on another device are not timed (and
+ * tct_timing_read then reports no timed call).
  */
 int tct_timing_enable(int on);
 

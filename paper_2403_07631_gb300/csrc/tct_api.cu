@@ -70,13 +70,24 @@ struct Timing {
     bool on = false;
     bool created = false;
     bool valid = false;
-    int phases = 0;
+    bool marks_ok = false;       // every event of the current call was recorded
+    int device = -1;             // the device the events belong to
     cudaEvent_t ev[4];
 };
 thread_local Timing g_timing;
 
+// Records phase event i of a timed call.  A call on another device than the
+// events' is not timed; a record that fails leaves the call untimed and its
+// error is cleared here (the launch errors before it were already taken).
 void mark(int i, cudaStream_t s) {
-    if (g_timing.on && g_timing.created) cudaEventRecord(g_timing.ev[i], s);
+    if (!g_timing.on || !g_timing.created) return;
+    if (i == 0) g_timing.marks_ok = true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g_timing.device ||
+        cudaEventRecord(g_timing.ev[i], s) != cudaSuccess) {
+        g_timing.marks_ok = false;
+        cudaGetLastError();
+    }
 }
 }  // namespace
 
@@ -263,7 +274,7 @@ int tct_build(const float *d_xyz, int64_t n, int32_t stride, const tct_grid *gri
     if (e == cudaSuccess) e = launch_elevations(*grid, ws, d_ground, d_ceil, s);
     mark(2, s);
     mark(3, s);
-    g_timing.valid = g_timing.on && e == cudaSuccess;
+    g_timing.valid = g_timing.on && g_timing.marks_ok && e == cudaSuccess;
     return cuda_status(e);
 }
 
@@ -290,7 +301,7 @@ int tct_evaluate(const tct_grid *grid, const tct_params *params, const float *d_
     mark(2, s);
     if (e == cudaSuccess) e = launch_chain(grid->n_slices, ws.upre, ws.ubits, params->flags, d_keep, st, s);
     mark(3, s);
-    g_timing.valid = g_timing.on && e == cudaSuccess;
+    g_timing.valid = g_timing.on && g_timing.marks_ok && e == cudaSuccess;
     return cuda_status(e);
 }
 
@@ -319,7 +330,7 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
     mark(2, s);
     if (e == cudaSuccess) e = launch_chain(grid->n_slices, ws.upre, ws.ubits, params->flags, d_keep, st, s);
     mark(3, s);
-    g_timing.valid = g_timing.on && e == cudaSuccess;
+    g_timing.valid = g_timing.on && g_timing.marks_ok && e == cudaSuccess;
     return cuda_status(e);
 }
 
@@ -371,6 +382,7 @@ int tct_build_evaluate_host(tct_host_io *io, int64_t n, int32_t stride, const tc
 
 int tct_timing_enable(int on) {
     if (on && !g_timing.created) {
+        if (cudaGetDevice(&g_timing.device) != cudaSuccess) return TCT_ERR_CUDA;
         for (int i = 0; i < 4; ++i)
             if (cudaEventCreate(&g_timing.ev[i]) != cudaSuccess) return TCT_ERR_CUDA;
         g_timing.created = true;
