@@ -6,6 +6,8 @@ query workloads, against the FP64 oracle.
   a CUDA graph and replayed, as the benchmark times it; every map's layers,
   masks, keep flags and statistics against the oracle run on that map alone
   (Sec. III-A/B/C per map).
+- the parking structure built, then evaluated on its layers: bit-identical
+  to the fused call.
 - 256 paths x 512 waypoints on the evaluated 5M-point parking structure: the
   cost / elevation queries and their adjoint (the C(q), e^G(q) of Eq. 10)
   against the oracle's values and analytic gradients, and the 50-step
@@ -99,7 +101,8 @@ def parking():
     og = oracle.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, z_min, sc.n_slices)
     xy = scenes.straight_paths(g["mask"][k] != 0, sc.x0, sc.y0, sc.res, 256, 512)
     sl = np.full(xy.shape[:2], k, np.int32)
-    return dict(grid=grid, og=og, cost=g["cost"], ground=g["ground"], xy=xy, sl=sl)
+    return dict(grid=grid, og=og, cost=g["cost"], ground=g["ground"], mask=g["mask"],
+                keep=g["keep"], stats=st, xy=xy, sl=sl)
 
 
 def _close(a, b, scale, what):
@@ -156,3 +159,22 @@ def test_paths_refinement_50_steps_full_size(parking):
         assert err.max() <= lim, f"step {s}: max error {err.max()} above {lim}"
     torch.cuda.synchronize()
     np.testing.assert_array_equal(fused.cpu().numpy(), stepped.cpu().numpy())
+
+
+def test_parking_build_then_evaluate_equals_fused(parking):
+    """The paper times construction and evaluation separately (Sec. IV-A):
+    tct_build then tct_evaluate on its layers (the incremental kernel in the
+    tile shape the benchmark's workload takes, with the given layers in place
+    of the pointer advance) give the fused call's costs, masks, keep flags
+    and per-slice counts bit for bit at full size (the fused outputs are
+    compared with the oracle in test_parity_gpu)."""
+    sc = scenes.parking_structure()
+    g_b, c_b, st_b = P.gpu_build(sc.points, _grid(sc))
+    z_min = float(st_b.z_min)
+    egrid = tct.Grid(sc.x0, sc.y0, sc.res, sc.W, sc.H, sc.d_s, sc.n_slices, z_min, False)
+    ev = P.gpu_evaluate(g_b, c_b, egrid, PARAMS_ROBOT, aux=False)
+    np.testing.assert_array_equal(g_b, parking["ground"])
+    np.testing.assert_array_equal(ev["cost"], parking["cost"])
+    np.testing.assert_array_equal(ev["mask"], parking["mask"])
+    np.testing.assert_array_equal(ev["keep"], parking["keep"])
+    assert ev["stats"].trav_cells[:sc.n_slices] == parking["stats"].trav_cells[:sc.n_slices]
