@@ -342,32 +342,46 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         int n_pass;
         if (given) {
             // given layers: this slice's ground and ceiling of the region,
-            // compared bit for bit with the previous slice's
+            // compared bit for bit with the previous slice's; four cells a
+            // thread at a time, so that their loads are in flight together
             int moved = 0;
             const float *gk = a.gin + (int64_t)k * HW, *ck = a.cin + (int64_t)k * HW;
-            for (int e = tid; e < G::NE; e += kNT) {
-                const int r = e / G::EW, s = e - r * G::EW;
-                const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
-                float g = -INFINITY, cz = INFINITY;
-                if (i >= 0 && i < a.H && j >= 0 && j < a.W) {
-                    const int64_t cell = (int64_t)i * a.W + j;
-                    g = gk[cell];
-                    cz = ck[cell];
+            constexpr int kLoad = 4;
+            for (int e0 = tid; e0 < G::NE; e0 += kLoad * kNT) {
+                float g[kLoad], cz[kLoad];
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) {
+                    const int e = e0 + u * kNT;
+                    const int r = e / G::EW, s = e - r * G::EW;
+                    const int i = ty0 - G::HE + r, j = tx0 - G::HE + s;
+                    g[u] = -INFINITY;
+                    cz[u] = INFINITY;
+                    if (e < G::NE && i >= 0 && i < a.H && j >= 0 && j < a.W) {
+                        const int64_t cell = (int64_t)i * a.W + j;
+                        g[u] = gk[cell];
+                        cz[u] = ck[cell];
+                    }
                 }
-                const float g0 = sEG[e], c0 = sZC[e];
-                const bool gch = __float_as_uint(g) != __float_as_uint(g0);
-                const bool cch = __float_as_uint(cz) != __float_as_uint(c0);
-                if (gch || cch) {
-                    moved = 1;
-                    sEG[e] = g;
-                    sZC[e] = cz;
-                    const uint32_t bit = 1u << (s & 31);
-                    if (gch) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
-                    if (cch) atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
-                    // a ground of the tile that falls: the run-based
-                    // uniqueness bits below assume grounds never fall
-                    if (g < g0 && r >= G::HE && r < G::HE + TH && s >= G::HE && s < G::HE + TW)
-                        *a.falls = 1;
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) {
+                    const int e = e0 + u * kNT;
+                    if (e >= G::NE) break;
+                    const int r = e / G::EW, s = e - r * G::EW;
+                    const float g0 = sEG[e], c0 = sZC[e];
+                    const bool gch = __float_as_uint(g[u]) != __float_as_uint(g0);
+                    const bool cch = __float_as_uint(cz[u]) != __float_as_uint(c0);
+                    if (gch || cch) {
+                        moved = 1;
+                        sEG[e] = g[u];
+                        sZC[e] = cz[u];
+                        const uint32_t bit = 1u << (s & 31);
+                        if (gch) atomicOr(&sChgG[r * G::EWW + (s >> 5)], bit);
+                        if (cch) atomicOr(&sChgC[r * G::EWW + (s >> 5)], bit);
+                        // a ground of the tile that falls: the run-based
+                        // uniqueness bits below assume grounds never fall
+                        if (g[u] < g0 && r >= G::HE && r < G::HE + TH && s >= G::HE && s < G::HE + TW)
+                            *a.falls = 1;
+                    }
                 }
             }
             n_pass = __syncthreads_or(moved);
