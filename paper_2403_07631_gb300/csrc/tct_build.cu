@@ -711,7 +711,7 @@ __device__ void block_sort_chunk(float *__restrict__ seg, int32_t n, float *buf)
 // Both queues in one launch: the blocks take the block-sort segments (from
 // the back of long_cells) in turn first, then their warps take the segments of
 // 17 .. kWarpSort heights (from the front), each sorted in a warp's registers.
-__global__ void __launch_bounds__(kHugeThreads, 2)
+__global__ void __launch_bounds__(kHugeThreads, 3)
 k_sort_queued(const int32_t *__restrict__ start, float *__restrict__ zs,
               float *__restrict__ scratch, const int32_t *__restrict__ long_count,
               const int32_t *__restrict__ long_cells, int64_t m) {
@@ -772,7 +772,7 @@ k_sort_queued(const int32_t *__restrict__ start, float *__restrict__ zs,
     }
 }
 
-// Blocks of the long-segment sorts: a resident wave (two blocks per SM).
+// Blocks of the long-segment sorts: a resident wave (three blocks per SM).
 int sm_count() {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -879,7 +879,7 @@ cudaError_t launch_partition(const float *xyz, int64_t n, int stride, const tct_
         const unsigned nbk = (unsigned)((m + (1 << blog) - 1) >> blog);
         k_bucket_sort<<<nbk, kThreads, 0, s>>>(ws.start, m, ws.bcur, ws.scratch, ws.bucket_l, ws.zs,
                                                ws.long_count, ws.long_cells, blog);
-        k_sort_queued<<<2 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+        k_sort_queued<<<3 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
                                                               ws.long_count, ws.long_cells, m);
     }
     count_launches((n > 0 ? 5 : 1) + scan_launches);
@@ -928,7 +928,7 @@ cudaError_t launch_partition_batched(const BatchPointsIn *maps, int n_maps, int 
                                                ws.long_count, ws.long_cells, blog);
         launches += 2;
     }
-    k_sort_queued<<<2 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
+    k_sort_queued<<<3 * sm_count(), kHugeThreads, 0, s>>>(ws.start, ws.zs, ws.scratch,
                                                           ws.long_count, ws.long_cells, m);
     count_launches(launches);
     return cudaGetLastError();
