@@ -36,7 +36,7 @@ Layout layout(const tct_grid &g, int64_t n_points) {
     L.upre = o; o = align_up(o + 4 * (TCT_MAX_SLICES + 1));
     L.ubits = o; o = align_up(o + 16 * (TCT_MAX_SLICES + 1));
     L.stats = o; o = align_up(o + sizeof(tct_stats));
-    L.queue = o; o = align_up(o + 4);
+    L.queue = o; o = align_up(o + 8);
     L.falls = o; o = align_up(o + 4);
     L.total = o;
     return L;
@@ -324,11 +324,14 @@ int tct_build_evaluate(const float *d_xyz, int64_t n, int32_t stride, const tct_
     mark(0, s);
     cudaError_t e = launch_partition(d_xyz, n, stride, *grid, ws, st, s);
     mark(1, s);
+    bool chained = false;       // the slice stack's last CTA ran the chain
     if (e == cudaSuccess)
         e = launch_stack(*grid, c, &ws, ws.zkeys, nullptr, nullptr, d_ground, d_ceil, d_cost,
-                         d_mask, nullptr, ws.upre, ws.ubits, st, s);
+                         d_mask, nullptr, ws.upre, ws.ubits, st, s, TCT_TILE_AUTO, nullptr,
+                         nullptr, d_keep, &chained);
     mark(2, s);
-    if (e == cudaSuccess) e = launch_chain(grid->n_slices, ws.upre, ws.ubits, params->flags, d_keep, st, s);
+    if (e == cudaSuccess && !chained)
+        e = launch_chain(grid->n_slices, ws.upre, ws.ubits, params->flags, d_keep, st, s);
     mark(3, s);
     g_timing.valid = g_timing.on && g_timing.marks_ok && e == cudaSuccess;
     return cuda_status(e);

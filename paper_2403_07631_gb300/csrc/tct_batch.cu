@@ -98,15 +98,7 @@ __global__ void k_batch_chain(const __grid_constant__ BatchSmall b) {
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    int p = -1, kept = 0;
-    for (int k = 0; k < N; ++k) {
-        const int row = p + 1;
-        bool u = row < s_pre[k] || ((s_bits[4 * k + (row >> 5)] >> (row & 31)) & 1u);
-        if ((m.flags & TCT_KEEP_ENDS) && (k == 0 || k == N - 1)) u = true;
-        m.keep[k] = u ? 1 : 0;
-        if (u) { p = k; ++kept; }
-    }
-    m.stats->n_kept = kept;
+    m.stats->n_kept = chain_walk(N, s_pre, s_bits, m.flags, m.keep);
     m.stats->z_min = key_float(m.zkeys[0]);
     m.stats->z_max = key_float(m.zkeys[1]);
 }

@@ -782,8 +782,8 @@ int sm_count() {
 
 // The statistics block starts from zero (the partition's passes add to it),
 // then takes the call's sizes; the z bounds start empty.  The slice stack's
-// uniqueness rows and tile queue of the same workspace are cleared here too,
-// a launch ahead of their use.
+// uniqueness rows, tile queue and count of finished CTAs of the same
+// workspace are cleared here too, a launch ahead of their use.
 __global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, int32_t n_slices,
                                  int32_t *upre, uint32_t *ubits, int32_t *queue) {
     int32_t *w = reinterpret_cast<int32_t *>(stats);
@@ -791,7 +791,7 @@ __global__ void k_partition_init(int32_t *zkeys, tct_stats *stats, int64_t n, in
         w[i] = 0;
     for (int i = threadIdx.x; i <= TCT_MAX_SLICES; i += blockDim.x) upre[i] = 0;
     for (int i = threadIdx.x; i < 4 * (TCT_MAX_SLICES + 1); i += blockDim.x) ubits[i] = 0;
-    if (threadIdx.x == 0) *queue = 0;
+    if (threadIdx.x == 0) queue[0] = queue[1] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         zkeys[0] = float_key(INFINITY);

@@ -29,6 +29,24 @@ __host__ __device__ __forceinline__ float key_float(int32_t k) {
 #endif
 }
 
+#ifdef __CUDACC__
+// The chain of Sec. III-C: slice k is kept when it is unique against the last
+// kept slice (uniqueness row p + 1: below pre[k], or its bit in bits[4 k ..]),
+// an end slice also with TCT_KEEP_ENDS.  One thread; returns the slices kept.
+__device__ __forceinline__ int chain_walk(int n_slices, const int32_t *pre, const uint32_t *bits,
+                                          uint32_t flags, uint8_t *keep) {
+    int p = -1, kept = 0;
+    for (int k = 0; k < n_slices; ++k) {
+        const int row = p + 1;
+        bool u = row < pre[k] || ((bits[4 * k + (row >> 5)] >> (row & 31)) & 1u);
+        if ((flags & TCT_KEEP_ENDS) && (k == 0 || k == n_slices - 1)) u = true;
+        keep[k] = u ? 1 : 0;
+        if (u) { p = k; ++kept; }
+    }
+    return kept;
+}
+#endif
+
 // Workspace carved from the caller's buffer; offsets are 256-byte aligned.
 struct Workspace {
     int32_t *cnt;       // [HW]   points per cell (zero between builds)
@@ -45,7 +63,8 @@ struct Workspace {
     int32_t *upre;      // [128]  per slice: bits [0, upre) of the uniqueness row set
     uint32_t *ubits;    // [128][4] per slice: further uniqueness bits
     tct_stats *stats;   // fallback stats block when the caller passes none
-    int32_t *queue;     // [1]    tile queue of the persistent slice-stack kernel
+    int32_t *queue;     // [2]    tile queue of the persistent slice-stack kernel, and its
+                        //        count of finished CTAs (the last one runs the chain)
     int32_t *falls;     // [1]    set when a given ground layer falls from a slice to the next
     size_t bytes;
 };
@@ -95,6 +114,8 @@ struct StackArgs {
     const float *zs;
     const float *gin, *cin;      // given layers (evaluate path)
     int32_t *falls;              // set by the kernel when a given ground falls
+    uint8_t *keep;               // with done: the chain runs in the stack kernel's last CTA
+    int32_t *done;               // finished CTAs (zero at launch)
     float *ground, *ceil, *cost, *aux;
     uint8_t *mask;
     int32_t *upre;
@@ -131,12 +152,16 @@ cudaError_t launch_elevations(const tct_grid &g, const Workspace &ws, float *gro
 // Given layers (lists NULL) run the incremental kernel too when it supports
 // the radii and no aux output is asked for; queue and falls are then that
 // call's tile queue and falling-ground flag.
+// keep: with lists, the keep flags the incremental kernel's last CTA writes
+// by the chain of Sec. III-C; *chained tells whether it did (otherwise the
+// caller launches the chain).
 cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace *lists,
                          const int32_t *zkeys, const float *gin, const float *cin,
                          float *ground, float *ceil, float *cost, uint8_t *mask, float *aux,
                          int32_t *upre, uint32_t *ubits, tct_stats *stats, cudaStream_t s,
                          int tile = TCT_TILE_AUTO, int32_t *queue = nullptr,
-                         int32_t *falls = nullptr);
+                         int32_t *falls = nullptr, uint8_t *keep = nullptr,
+                         bool *chained = nullptr);
 // The incremental kernel for the build path; returns cudaErrorNotSupported
 // when no instance matches the window radii (the caller then falls back).
 // tile: one of the TCT_TILE_* shapes.

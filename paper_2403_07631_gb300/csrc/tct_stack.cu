@@ -338,17 +338,7 @@ __global__ void k_chain(int n_slices, const int32_t *upre, const uint32_t *ubits
         s_bits[4 * k + 3] = ubits[4 * k + 3];
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    int p = -1;
-    int kept = 0;
-    for (int k = 0; k < n_slices; ++k) {
-        const int row = p + 1;
-        bool u = row < s_pre[k] || ((s_bits[4 * k + (row >> 5)] >> (row & 31)) & 1u);
-        if ((flags & TCT_KEEP_ENDS) && (k == 0 || k == n_slices - 1)) u = true;
-        keep[k] = u ? 1 : 0;
-        if (u) { p = k; ++kept; }
-    }
-    stats->n_kept = kept;
+    if (threadIdx.x == 0) stats->n_kept = chain_walk(n_slices, s_pre, s_bits, flags, keep);
 }
 
 // Given layers whose ground falls somewhere from one slice to the next (not
@@ -453,7 +443,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
                          const int32_t *zkeys, const float *gin, const float *cin, float *ground,
                          float *ceil, float *cost, uint8_t *mask, float *aux, int32_t *upre,
                          uint32_t *ubits, tct_stats *stats, cudaStream_t s, int tile,
-                         int32_t *queue, int32_t *falls) {
+                         int32_t *queue, int32_t *falls, uint8_t *keep, bool *chained) {
     StackArgs a;
     a.W = g.W;
     a.H = g.H;
@@ -476,11 +466,24 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.stats = stats;
     a.c = c;
     a.falls = falls;
+    a.keep = nullptr;
+    a.done = nullptr;
+    if (chained) *chained = false;
     if (lists) {
-        // the partition of this workspace has cleared its uniqueness rows and queue
+        // the partition of this workspace has cleared its uniqueness rows,
+        // queue and count of finished CTAs
+        if (keep) {
+            a.keep = keep;
+            a.done = lists->queue + 1;
+        }
         if (tile == TCT_TILE_AUTO && inc_supported(c, a.N)) tile = choose_tile(c, 1, &a, 1);
         const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
-        if (e != cudaErrorNotSupported) return e;
+        if (e != cudaErrorNotSupported) {
+            if (chained) *chained = e == cudaSuccess && keep != nullptr;
+            return e;
+        }
+        a.keep = nullptr;
+        a.done = nullptr;
         return pick_tile<true, false>(a, s);
     }
     k_stack_init<<<1, 128, 0, s>>>(upre, ubits, queue, falls);

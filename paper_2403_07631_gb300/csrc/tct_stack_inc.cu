@@ -19,7 +19,7 @@ IncMap inc_map(const StackArgs &a) {
     m.cin = a.start ? nullptr : a.cin;
     m.falls = a.falls;
     m.ground = a.ground; m.ceil = a.ceil; m.cost = a.cost; m.mask = a.mask;
-    m.upre = a.upre; m.ubits = a.ubits; m.stats = a.stats;
+    m.upre = a.upre; m.ubits = a.ubits; m.stats = a.stats; m.keep = a.keep;
     return m;
 }
 
@@ -123,6 +123,11 @@ cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArg
     b.c = c;
     b.n_maps = n_maps;
     b.queue = queue;
+    // the chain runs in the last CTA when every map has its keep flags and
+    // the first map brings the counter of finished CTAs
+    b.done = maps[0].done;
+    for (int i = 0; i < n_maps; ++i)
+        if (!maps[i].keep) b.done = nullptr;
     int TW, TH;
     tile_dims(tile, &TW, &TH);
     int total = 0;

@@ -150,6 +150,7 @@ struct IncMap {
     int32_t *upre;
     uint32_t *ubits;
     tct_stats *stats;
+    uint8_t *keep;               // keep flags the last CTA writes (with BatchArgs::done)
 };
 
 // One tile (TW x TH cells at tx0, ty0) of one map over all its slices, by
@@ -788,6 +789,8 @@ struct BatchArgs {
     int32_t n_maps;
     int32_t total;                       // items
     int32_t *queue;                      // next item (zero before the launch)
+    int32_t *done;                       // finished CTAs (zero before the launch); when set,
+                                         // the last CTA runs every map's chain
     int32_t item_start[TCT_MAX_BATCH + 1];
     int32_t tiles_x[TCT_MAX_BATCH];
     IncMap maps[TCT_MAX_BATCH];
@@ -811,6 +814,33 @@ k_stack_batched(const __grid_constant__ BatchArgs b) {
         const int tx = t % b.tiles_x[m], ty = t / b.tiles_x[m];
         stack_tile<RK, RP, TW, TH, KS>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
         __syncthreads();
+    }
+    if (b.done) {
+        // the chain of Sec. III-C, once every tile's uniqueness bits are in: the
+        // CTA that finishes last (its writes and the others' ordered before its
+        // count by the fences) reads the rows through L2 and walks them
+        __shared__ int32_t s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(b.done, 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            int32_t *s_pre = reinterpret_cast<int32_t *>(smem);     // the tile state is free now
+            uint32_t *s_bits = reinterpret_cast<uint32_t *>(s_pre + TCT_MAX_SLICES + 1);
+            for (int m = 0; m < b.n_maps; ++m) {
+                const IncMap &mp = b.maps[m];
+                for (int k = threadIdx.x; k < mp.N; k += blockDim.x) {
+                    s_pre[k] = __ldcg(mp.upre + k);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) s_bits[4 * k + w] = __ldcg(mp.ubits + 4 * k + w);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    mp.stats->n_kept = chain_walk(mp.N, s_pre, s_bits, b.c.flags, mp.keep);
+                __syncthreads();
+            }
+        }
     }
 }
 
