@@ -116,6 +116,7 @@ struct StackArgs {
     int32_t *falls;              // set by the kernel when a given ground falls
     uint8_t *keep;               // with done: the chain runs in the stack kernel's last CTA
     int32_t *done;               // finished CTAs (zero at launch)
+    int32_t split;               // slice ranges per tile (0 or 1: one; single-map build path)
     float *ground, *ceil, *cost, *aux;
     uint8_t *mask;
     int32_t *upre;

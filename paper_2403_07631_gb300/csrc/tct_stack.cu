@@ -384,6 +384,49 @@ k_uniq_general(const int32_t *falls, int64_t HW, int N, const float *__restrict_
         if (s_bits[i]) atomicOr(&ubits[i], s_bits[i]);
 }
 
+// The uniqueness rows of Sec. III-C for maps of up to kColSlices slices,
+// straight from the finished layers (the same tests as k_uniq_general: Eq. 9
+// against slice k+1, Eq. 8 against every earlier slice p): a thread holds its
+// cell's column of grounds and costs, loaded at once, and a warp's rows leave
+// with one shared atomic per slice.  The rows fit the first word of each
+// slice's bits (p + 1 < 32).
+constexpr int kColSlices = 16;
+
+__global__ void __launch_bounds__(256)
+k_uniq_columns(int64_t HW, int N, const float *__restrict__ ground,
+               const float *__restrict__ cost, float c_b, uint32_t *ubits) {
+    __shared__ uint32_t s_bits[kColSlices];
+    if (threadIdx.x < kColSlices) s_bits[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < HW;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = base + lane;
+        const bool live = cell < HW;
+        float g[kColSlices], ct[kColSlices];
+#pragma unroll
+        for (int k = 0; k < kColSlices; ++k) {
+            g[k] = live && k < N ? ground[(int64_t)k * HW + cell] : 0.0f;
+            ct[k] = live && k < N ? cost[(int64_t)k * HW + cell] : INFINITY;
+        }
+#pragma unroll
+        for (int k = 0; k < kColSlices; ++k) {
+            const int kn = k + 1 < kColSlices ? k + 1 : k;   // slice k + 1 (read when k + 1 < N)
+            uint32_t row = 0;
+            if (k < N && ct[k] < c_b && (k + 1 >= N || g[kn] - g[k] > 0.0f || ct[k] < ct[kn])) {
+                row = 1u;                                // row 0: no slice kept yet
+#pragma unroll
+                for (int p = 0; p < k; ++p)
+                    if (g[k] - g[p] > 0.0f || ct[k] < ct[p]) row |= 1u << (p + 1);
+            }
+            row = __reduce_or_sync(0xffffffffu, row);
+            if (lane == 0 && row) atomicOr(&s_bits[k], row);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < N && s_bits[threadIdx.x]) atomicOr(&ubits[4 * threadIdx.x], s_bits[threadIdx.x]);
+}
+
 __global__ void k_stack_init(int32_t *upre, uint32_t *ubits, int32_t *queue, int32_t *falls) {
     const int i = threadIdx.x;
     if (i == 0 && queue) *queue = 0;
@@ -468,6 +511,7 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
     a.falls = falls;
     a.keep = nullptr;
     a.done = nullptr;
+    a.split = 1;
     if (chained) *chained = false;
     if (lists) {
         // the partition of this workspace has cleared its uniqueness rows,
@@ -477,10 +521,28 @@ cudaError_t launch_stack(const tct_grid &g, const EvalConsts &c, const Workspace
             a.done = lists->queue + 1;
         }
         if (tile == TCT_TILE_AUTO && inc_supported(c, a.N)) tile = choose_tile(c, 1, &a, 1);
+        // A small map (32 x 32 tiles, fewer than the SMs) of a few slices is a
+        // latency chain of its slices: each tile's slices are cut into ranges
+        // of at least four, one CTA each, so that more SMs walk shorter chains;
+        // the uniqueness rows then come from the finished layers.
+        const int64_t HW = (int64_t)a.W * a.H;
+        if (tile == TCT_TILE_32 && a.N >= 8 && a.N <= kColSlices) {
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t tiles = (int64_t)((a.W + 31) / 32) * ((a.H + 31) / 32);
+            a.split = (int)std::min<int64_t>(a.N / 4, std::max<int64_t>(1, sms / tiles));
+        }
         const cudaError_t e = launch_stack_inc(a, lists->queue, tile, s);
         if (e != cudaErrorNotSupported) {
-            if (chained) *chained = e == cudaSuccess && keep != nullptr;
-            return e;
+            if (e != cudaSuccess || a.split <= 1) {
+                if (chained) *chained = e == cudaSuccess && keep != nullptr;
+                return e;
+            }
+            const int blocks = (int)std::min<int64_t>((HW + 255) / 256, 4096);
+            k_uniq_columns<<<blocks, 256, 0, s>>>(HW, a.N, ground, cost, c.c_b, ubits);
+            count_launches(1);
+            return cudaGetLastError();      // the caller launches the chain
         }
         a.keep = nullptr;
         a.done = nullptr;

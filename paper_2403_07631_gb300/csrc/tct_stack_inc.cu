@@ -128,6 +128,10 @@ cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArg
     b.done = maps[0].done;
     for (int i = 0; i < n_maps; ++i)
         if (!maps[i].keep) b.done = nullptr;
+    // a single map's tiles may be cut into slice ranges (the uniqueness rows
+    // then come from a pass over the finished layers, and the chain after it)
+    b.split = n_maps == 1 && maps[0].split > 1 ? maps[0].split : 1;
+    if (b.split > 1) b.done = nullptr;
     int TW, TH;
     tile_dims(tile, &TW, &TH);
     int total = 0;
@@ -135,7 +139,7 @@ cudaError_t launch_stack_batched(const EvalConsts &c, int n_maps, const StackArg
         b.maps[i] = inc_map(maps[i]);
         b.item_start[i] = total;
         b.tiles_x[i] = (maps[i].W + TW - 1) / TW;
-        total += b.tiles_x[i] * ((maps[i].H + TH - 1) / TH);
+        total += b.tiles_x[i] * ((maps[i].H + TH - 1) / TH) * b.split;
     }
     b.item_start[n_maps] = total;
     b.total = total;

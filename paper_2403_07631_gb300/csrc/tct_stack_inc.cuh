@@ -153,12 +153,17 @@ struct IncMap {
     uint8_t *keep;               // keep flags the last CTA writes (with BatchArgs::done)
 };
 
-// One tile (TW x TH cells at tx0, ty0) of one map over all its slices, by
-// one CTA of Geo::NT threads.  smem is the dynamic buffer of smem_bytes();
-// the caller synchronises before the buffer is used for another tile.
+// One tile (TW x TH cells at tx0, ty0) of one map over its slices
+// [k_begin, k_end), by one CTA of Geo::NT threads.  smem is the dynamic buffer
+// of smem_bytes(); the caller synchronises before the buffer is used for
+// another tile.  The first slice of the range is computed in full (as slice 0
+// always is), so a range may start anywhere; the uniqueness rows are
+// accumulated only when uniq is set (the whole slice range), otherwise they
+// are left to a pass over the finished layers.
 template <int RK, int RP, int TW, int TH, int KS>
 __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c, int tx0, int ty0,
-                                           unsigned char *smem, SliceCounters &counters) {
+                                           unsigned char *smem, SliceCounters &counters,
+                                           int k_begin, int k_end, bool uniq) {
     using G = Geo<RK, RP, TW, TH, KS>;
     constexpr int kStrip = KS;             // rows of a thread's inflation strip
     constexpr int kNT = G::NT, kNW = G::NW;
@@ -322,8 +327,8 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     };
     __syncthreads();
 
-    for (int k = 0; k < a.N; ++k) {
-        const bool first = k == 0;
+    for (int k = k_begin; k < k_end; ++k) {
+        const bool first = k == k_begin;
         const float h = __fmaf_rn((float)(k + 1), a.d_s, z_min);
         uint32_t *sChgG = sChgG0 + (k & 1) * G::EH * G::EWW;
         uint32_t *sChgC = sChgC0 + (k & 1) * G::EH * G::EWW;
@@ -664,23 +669,26 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
         if (need_simp) {
             // Eq. 9 of slice k-1 against slice k, then the rows p it is unique against
             int pre = 0;
-            uint32_t walk = 0;
+            if (uniq) {
+                uint32_t walk = 0;
 #pragma unroll
-            for (int q = 0; q < kStrip; ++q) {
-                const bool gq = (gchbits >> q) & 1u;
-                if (!first && ((inmap >> q) & 1u) && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
-                    if (!((runle >> q) & 1u)) walk |= 1u << q;
-                    pre = max(pre, run_get(q) + 1);
+                for (int q = 0; q < kStrip; ++q) {
+                    const bool gq = (gchbits >> q) & 1u;
+                    if (!first && ((inmap >> q) & 1u) && cT[q] < c.c_b && (gq || cT[q] < acc[q])) {
+                        if (!((runle >> q) & 1u)) walk |= 1u << q;
+                        pre = max(pre, run_get(q) + 1);
+                    }
                 }
+                if (!first) mark_run(walk, k - 1);
             }
-            if (!first) mark_run(walk, k - 1);
 #pragma unroll
             for (int q = 0; q < kStrip; ++q) {
                 const uint32_t bit = 1u << q;
-                if (gchbits & bit) {
+                // the run state the uniqueness walks use
+                if (uniq && (gchbits & bit)) {
                     run_set(q, k);
                     runle |= bit;
-                } else if (!first) {
+                } else if (uniq && !first) {
                     // the run now covers slice k-1 (cost cT) and the current cost is acc
                     if (runle & bit) {
                         // no earlier cost of the run exceeded cT, so the run's
@@ -701,7 +709,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
                 cT[q] = acc[q];
             }
             const int wmax = __reduce_max_sync(0xffffffffu, pre);
-            if (lane == 0 && wmax > 0) atomicMax(&s_upre[k - 1], wmax);
+            if (lane == 0 && wmax > 0) atomicMax(&s_upre[k - 1], wmax);   // 0 unless uniq
             travbits = 0;
 #pragma unroll
             for (int q = 0; q < kStrip; ++q)
@@ -739,7 +747,7 @@ __device__ __forceinline__ void stack_tile(const IncMap &a, const EvalConsts &c,
     }
 
     // Eq. 9 holds vacuously for the last slice
-    {
+    if (uniq) {
         int pre = 0;
         uint32_t walk = 0;
 #pragma unroll
@@ -791,6 +799,8 @@ struct BatchArgs {
     int32_t *queue;                      // next item (zero before the launch)
     int32_t *done;                       // finished CTAs (zero before the launch); when set,
                                          // the last CTA runs every map's chain
+    int32_t split;                       // slice ranges per tile (1: the whole stack, with the
+                                         // uniqueness rows; more: items of one range each)
     int32_t item_start[TCT_MAX_BATCH + 1];
     int32_t tiles_x[TCT_MAX_BATCH];
     IncMap maps[TCT_MAX_BATCH];
@@ -810,9 +820,15 @@ k_stack_batched(const __grid_constant__ BatchArgs b) {
         if (item >= b.total) break;
         int m = 0;
         while (m + 1 < b.n_maps && b.item_start[m + 1] <= item) ++m;
-        const int t = item - b.item_start[m];
+        const int t = (item - b.item_start[m]) / b.split, rg = (item - b.item_start[m]) % b.split;
         const int tx = t % b.tiles_x[m], ty = t / b.tiles_x[m];
-        stack_tile<RK, RP, TW, TH, KS>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters);
+        const int N = b.maps[m].N;
+        // only the small-map shape is ever cut into slice ranges; the others
+        // keep the uniqueness rows as a compile-time constant
+        constexpr bool kMaySplit = TW == 32 && TH == 32;
+        stack_tile<RK, RP, TW, TH, KS>(b.maps[m], b.c, tx * TW, ty * TH, smem, counters,
+                                       (N * rg) / b.split, (N * (rg + 1)) / b.split,
+                                       !kMaySplit || b.split == 1);
         __syncthreads();
     }
     if (b.done) {
